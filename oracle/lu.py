@@ -76,9 +76,13 @@ def equilibrate_pow2(A):
     return R, S
 
 
-def fp16_mu():
-    """mu = largest power of two not above theta * xmax(fp16), theta = 0.1."""
-    return float(2.0 ** np.floor(np.log2(FP16_THETA * 65504.0)))
+def fp16_mu(n=1):
+    """mu = largest power of two not above theta * xmax(fp16) / sqrt(n), theta = 0.1.
+
+    The 1/sqrt(n) leaves room for the element growth of partial pivoting, which grows with
+    the dimension, so the factors do not overflow fp16 (a reading: the paper does not scale).
+    """
+    return float(2.0 ** np.floor(np.log2(FP16_THETA * 65504.0 / np.sqrt(n))))
 
 
 def scale_for(A, fmt):
@@ -86,7 +90,7 @@ def scale_for(A, fmt):
     n = A.shape[0]
     if fmt == "fp16":
         R, S = equilibrate_pow2(A)
-        return R, S, fp16_mu()
+        return R, S, fp16_mu(n)
     return np.ones(n), np.ones(n), 1.0
 
 

@@ -113,7 +113,7 @@ def test_fp16_scaling():
     assert np.all((np.abs(RA).max(axis=1) >= 0.5) & (np.abs(RA).max(axis=1) < 1.0))
     RAS = RA * S[None, :]
     assert np.all((np.abs(RAS).max(axis=0) >= 0.5) & (np.abs(RAS).max(axis=0) < 1.0))
-    assert lum.fp16_mu() == 4096.0
+    assert lum.fp16_mu(1) == 4096.0 and lum.fp16_mu(64) == 512.0 and lum.fp16_mu(16384) == 32.0
     F = lum.lu_block(A, "fp16", w=16)
     # without the scaling the entries (~1e9) would overflow fp16; with it M^-1 A ~ I
     X = np.stack([lum.apply_minv(F, A[:, j]) for j in range(64)], axis=1)
