@@ -1,0 +1,347 @@
+"""Benchmark: milliseconds to a normwise relative backward error <= 1e-15 for a dense n = 16384
+system with recycled mixed-precision GMRES-IR (BF16 tensor-core LU, FP64 working precision and
+residual, GCRO-DR(50, 10)), on synthetic randsvd matrices (geometric singular values, kappa_2 = 1e2).
+
+One step = the whole hot path on one system: gir_factor (scaling, u_f LU, diagonal-block
+inverses) + gir_solve (x0, refinement steps with FP64 residuals, GCRO-DR corrections) with
+A and b already resident in HBM. `e2e` times the same call sequence through the C ABI with
+the inputs in pinned host memory and the host<->device copies inside the timed region.
+The CPU oracle is timed on a bounded sample (a smaller system of the same family) and scaled
+by n^3 to the benchmark size.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms to 1e-15 rel. backward error, n=16384: recycled GMRES-IR vs FP64 LU"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(n_s=2048, kappa=1e2, uf="bf16"):
+    """The CPU oracle (as it stands) on one system of the benchmark family at size n_s."""
+    import numpy as np
+    from oracle.ir import Params as OP, solve as osolve
+    from synth import randsvd, normal_vector
+    A = randsvd(n_s, kappa, seed=0)
+    b = A @ normal_vector(n_s, 2)
+    t = time.perf_counter()
+    x, info, _, _ = osolve(A, b, OP(uf=uf, u="fp64", ur="fp64", ua="u", m=50, k=10, tau=1e-8, imax=10,
+                                    target=1e-15, lu_w=32))
+    dt = time.perf_counter() - t
+    return dt, info
+
+
+def cpu_baseline_json(n, n_s, kappa, uf):
+    dt, info = oracle_sample(n_s, kappa, uf)
+    scale = (n / n_s) ** 3
+    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle RGMRES-IR (numpy FP64, u_f by rounding) on randsvd n={n_s}, kappa_2={kappa:g}, "
+                      f"{uf}, GCRO-DR(50,10): {dt:.2f} s measured ({info.paper_format()}), scaled by "
+                      f"(n/{n_s})^3 = {scale:.0f} to n={n}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_s = args.sample_n
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(max(256, n_s // 4), args.kappa, args.uf)
+    for _ in range(args.steps):
+        dt, info = oracle_sample(n_s, args.kappa, args.uf)
+        vals.append(dt * 1e3 * (args.n / n_s) ** 3)
+    v = statistics.median(vals)
+    cb = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"oracle RGMRES-IR on randsvd n={n_s} per step, scaled by (n/{n_s})^3 to n={args.n}"}
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_json(args, world), "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def config_json(args, world):
+    return {"workload": f"randsvd dense n={args.n}, kappa_2={args.kappa:g}, b=A x*, x*~N(0,1); "
+                        f"u_f={args.uf} LU (tcgen05), u=fp64, u_r=fp64, GCRO-DR(m={args.m},k={args.k}), tau=1e-8, "
+                        f"target berr 1e-15",
+            "n": args.n, "kappa_2": args.kappa, "uf": args.uf, "u": "fp64", "ur": "fp64", "m": args.m, "k": args.k,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (A is 8n^2 bytes = 2.15 GB at n=16384)"}
+
+
+# algorithmic bytes / flops per launch of the phases the trace reports
+def roofline_for(phase, total_ms, calls, args, peaks, peak_kind):
+    n = args.n
+    if phase == "gemv":
+        per = 8.0 * n * n + 16.0 * n
+        unit, bound, pk = "GB/s", "hbm", peaks["hbm_gbs"]
+        achieved = per / ((total_ms / calls) * 1e-3) / 1e9
+    elif phase == "minv":
+        per = 2.0 * n * n + 48.0 * n          # L and U (16-bit, n^2 entries in all) + vectors
+        unit, bound, pk = "GB/s", "hbm", peaks["hbm_gbs"]
+        achieved = per / ((total_ms / calls) * 1e-3) / 1e9
+    elif phase == "residual":
+        per = 8.0 * n * n + 24.0 * n
+        unit, bound, pk = "GB/s", "hbm", peaks["hbm_gbs"]
+        achieved = per / ((total_ms / calls) * 1e-3) / 1e9
+    elif phase == "lu outer gemm":
+        nb = 256
+        fl = 0.0
+        c = nb
+        while c < n:
+            fl += 2.0 * (n - c) * (n - c) * nb
+            c += nb
+        per = fl / max(calls, 1)
+        unit, bound, pk = "TFLOP/s", "tensor", peaks["bf16_tflops"]
+        achieved = per / ((total_ms / calls) * 1e-3) / 1e12
+    else:
+        return None
+    return {"kernel": phase, "bound": bound, "achieved": achieved, "peak": pk, "unit": unit,
+            "frac": achieved / pk, "traffic": None, "peak_source": peak_kind,
+            "per_launch": per, "launches": calls, "avg_ms": total_ms / calls}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--kappa", type=float, default=1e2)
+    ap.add_argument("--uf", default="bf16")
+    ap.add_argument("--m", type=int, default=50)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--sample-n", type=int, default=2048)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-lu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2201_09827_gb300 as gir
+    from synth import randsvd_torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = load_peaks()
+
+    n = args.n
+    A = randsvd_torch(n, args.kappa, seed=rank, device=f"cuda:{local}")
+    g = torch.Generator(device=dev)
+    g.manual_seed(2 + 100 * rank)
+    xstar = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    b = A @ xstar
+    prm = gir.Params(uf=args.uf, u="fp64", ur="fp64", m=args.m, k=args.k, tau=1e-8, imax=10, target_berr=1e-15,
+                     carry_mode=1)
+
+    def step(Ad, bd, x):
+        F = gir.Factorization(Ad, prm)
+        _, info = F.solve(Ad, bd, x)
+        F.close()
+        return info
+
+    x = torch.empty_like(b)
+    for _ in range(args.warmup):
+        info = step(A, b, x)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- timed region (device-resident inputs) ----------------
+    gir.trace_enable(True)
+    l0 = gir.launch_count()
+    times, infos = [], []
+    with ClockSampler(local) as clk:
+        barrier()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step(A, b, x)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        barrier()
+    launches = gir.launch_count() - l0
+    trace = gir.trace_report()
+    gir.trace_enable(False)
+    clocks = clk.summary()
+
+    # correctness of the timed result: backward error from a double-double residual
+    r = gir.residual(A, x, b, "dd")
+    eta = (r.abs().max() / (A.abs().sum(1).max() * x.abs().max() + b.abs().max())).item()
+    ms = statistics.median(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+
+    # ---------------- end to end through the C ABI with host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        Ah = A.cpu().pin_memory()
+        bh = b.cpu().pin_memory()
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        Ad = torch.empty_like(A)
+        bd = torch.empty_like(b)
+        xd = torch.empty_like(b)
+        et = []
+        for it in range(max(2, args.steps // 2) + 1):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Ad.copy_(Ah, non_blocking=True)
+            bd.copy_(bh, non_blocking=True)
+            step(Ad, bd, xd)
+            xh.copy_(xd, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if it > 0:
+                et.append(e0.elapsed_time(e1))
+        e2e = {"value": statistics.median(et), "unit": "ms", "h2d_bytes_per_step": 8 * n * n + 8 * n,
+               "d2h_bytes_per_step": 8 * n}
+        del Ad, bd, xd, Ah
+
+    # ---------------- FP64 LU comparator on the same GPU (library, context) ----------------
+    fp64_lu_ms = None
+    if not args.no_fp64_lu and rank == 0:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xl = torch.linalg.solve(A, b)
+        e1.record(stream)
+        e1.synchronize()
+        fp64_lu_ms = e0.elapsed_time(e1)
+        del xl
+
+    # ---------------- roofline of the dominant phase ----------------
+    roof = None
+    if trace:
+        known = {k: v for k, v in trace.items() if k in ("gemv", "minv", "residual", "lu outer gemm")}
+        if known:
+            dom = max(known, key=lambda k: known[k][0])
+            roof = roofline_for(dom, known[dom][0], known[dom][1], args, peaks, peak_kind)
+    phase_ms = {k: round(v[0] / args.steps, 3) for k, v in sorted(trace.items(), key=lambda kv: -kv[1][0])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_json(n, args.sample_n, args.kappa, args.uf)
+
+    if rank == 0:
+        last = infos[-1]
+        out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_json(args, world),
+               "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+               "result": {"status": last.status, "its": last.its, "total_its": last.total_its,
+                          "ir_steps": last.ir_steps, "berr_dd": eta, "ms_factor": last.ms_factor,
+                          "ms_solve": last.ms_solve, "times_ms": times},
+               "fp64_lu_ms": fp64_lu_ms, "phase_ms_per_step": phase_ms}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

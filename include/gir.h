@@ -1,0 +1,204 @@
+/*
+ * gir.h -- C ABI of the GB300 (sm_103a) recycled mixed-precision GMRES-IR solver.
+ *
+ * The method is RGMRES-IR (Oktay & Carson, "Mixed Precision GMRES-based Iterative
+ * Refinement with Recycling", Algorithm 4): a low-precision (u_f) LU factorization with
+ * partial pivoting, refinement steps whose residual r_i = b - A x_i is computed in
+ * precision u_r, and a correction equation U^-1 L^-1 A d = U^-1 L^-1 r_i solved by
+ * GCRO-DR(m, k) (Algorithm 3), whose recycle space U_k, C_k is carried from one
+ * refinement step to the next. With k = 0 the same code is GMRES-IR (Algorithm 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrix and vector pointers are DEVICE pointers owned by the caller unless a
+ *    parameter says otherwise; matrices are FP64, row-major, leading dimension lda >= n.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). All work
+ *    is enqueued on it; entry points that return numbers to the host (gir_info, status)
+ *    synchronise that stream before returning.
+ *  - Errors are returned as gir_status, never thrown across the ABI. On any status other
+ *    than GIR_OK / GIR_NOT_CONVERGED the output buffers are unspecified.
+ *  - Not thread-safe per handle: one call at a time per gir_handle.
+ */
+#ifndef GIR_H
+#define GIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Precisions (Table 1; bf16 and fp8-e4m3 are the formats Section 3 mentions as
+ * alternatives to the IEEE ones; GIR_DD is double-double, standing in for quad). */
+typedef enum {
+    GIR_FP64 = 0,
+    GIR_FP32 = 1,
+    GIR_FP16 = 2,
+    GIR_BF16 = 3,
+    GIR_FP8_E4M3 = 4,
+    GIR_DD = 5
+} gir_prec;
+
+typedef enum {
+    GIR_OK = 0,
+    GIR_NOT_CONVERGED = 1,  /* i_max refinement steps without meeting the stop test (the paper's "-") */
+    GIR_SINGULAR = 2,       /* a zero pivot in the u_f factorization */
+    GIR_NONFINITE = 3,      /* Inf/NaN in the input, the factors or an iterate */
+    GIR_INVALID_ARG = 4,
+    GIR_TIMEOUT = 5,        /* a bounded device-side wait gave up (no hang) */
+    GIR_CUDA_ERROR = 6,
+    GIR_OOM = 7,
+    GIR_UNSUPPORTED = 8     /* a precision combination this build does not implement */
+} gir_status;
+
+/* Arguments of Algorithm 4's "Require" line plus the readings the paper leaves open. */
+typedef struct {
+    gir_prec uf;        /* factorization precision u_f: GIR_FP16 (scaled), GIR_BF16, GIR_FP8_E4M3 */
+    gir_prec u;         /* working precision u (storage of x, d, Krylov vectors): GIR_FP64 or GIR_FP32 */
+    gir_prec ur;        /* residual precision u_r: GIR_FP64 or GIR_DD */
+    gir_prec ua;        /* precision of the A~ = M^-1 A application: GIR_FP64 (Section 4.3.1 uniform
+                           precision when u = FP64, u^2 when u = FP32) */
+    int m;              /* GCRO-DR restart length (maximum subspace size), 1 <= m <= GIR_MAX_M */
+    int k;              /* recycle dimension, 0 <= k < m; k = 0 gives GMRES-IR(m) */
+    double tau;         /* inner tolerance on the relative preconditioned residual */
+    int imax;           /* maximum number of refinement steps */
+    double target_berr; /* stop when ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= target_berr;
+                           a negative value selects 2*u; 0 runs exactly imax steps */
+    int carry_mode;     /* 0: recompute QR(A~ Y~) at each new refinement step (Algorithm 3, lines 1-4);
+                           1: reuse (U_k, C_k), which satisfy A~ U_k = C_k already */
+    int max_its;        /* cap on Arnoldi steps per GCRO-DR call (<= 0: 20*m) */
+    int lu_nb;          /* LU outer block width (<= 0: default) */
+    unsigned flags;     /* reserved, must be 0 */
+} gir_params;
+
+#define GIR_MAX_M 112
+#define GIR_MAX_K 64
+#define GIR_MAX_IR 64
+
+typedef struct {
+    gir_status status;
+    int ir_steps;               /* number of GCRO-DR calls (refinement steps) */
+    int total_its;              /* sum of Arnoldi steps over all refinement steps */
+    int its[GIR_MAX_IR];        /* Arnoldi steps per refinement step (the paper's per-step counts) */
+    int carry_applies[GIR_MAX_IR];
+    double berr[GIR_MAX_IR + 1];/* eta_i = ||r_i||_inf / (||A||_inf ||x_i||_inf + ||b||_inf), i = 0..ir_steps */
+    double final_berr;
+    int cycles;                 /* GCRO-DR restart cycles over all steps */
+    int k_eff;                  /* recycle dimension at exit */
+    float ms_factor;            /* device time of gir_factor (CUDA events) */
+    float ms_solve;             /* device time of the refinement loop */
+} gir_info;
+
+typedef struct gir_handle gir_handle;
+
+/* Algorithm 4, line 1: factor P (mu R A S) = L U in precision u_f with partial pivoting.
+ * A: device, n x n row-major, lda >= n; read only, not retained.
+ * Allocates the handle (factors, pivots, scalings, recycle space, workspaces); *out owns it.
+ * Returns GIR_SINGULAR on a zero pivot, GIR_NONFINITE on overflow, GIR_OOM. Synchronises. */
+gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params* params,
+                      void* stream, gir_handle** out);
+
+/* Algorithm 4, lines 2-8: x0 = M^-1 b, then refinement steps with GCRO-DR corrections.
+ * A: the same FP64 matrix that was factored (needed for the residual in u_r, line 4).
+ * b: device n-vector; x: device n-vector (output). info: host struct (may be NULL).
+ * The recycle space persists in the handle: later calls with new b start from it (Section 2).
+ * Returns GIR_OK, GIR_NOT_CONVERGED (x holds the last iterate), GIR_NONFINITE, GIR_TIMEOUT. */
+gir_status gir_solve(gir_handle* h, const double* A, int64_t lda, const double* b, double* x,
+                     gir_info* info, void* stream);
+
+/* Adjoint solve A^T lambda = g by the same refinement, left-preconditioned with M^T
+ * (operator M^-T A^T), reusing the factors of gir_factor. Keeps its own recycle space,
+ * seeded from the forward U_k when the adjoint one is empty. Not in the paper (used for
+ * gradients: db = lambda, dA = -lambda x^T). Same arguments and statuses as gir_solve. */
+gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const double* g,
+                             double* lambda, gir_info* info, void* stream);
+
+/* Batch of independent systems A_i x_i = b_i of different sizes n[i] (host array), each
+ * with its own factorization and recycle space. A, b, x: host arrays of device pointers.
+ * infos: host array of nsys entries (may be NULL). Returns the worst status. Not in the paper. */
+gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
+                           const double* const* b, double* const* x, const gir_params* params,
+                           gir_info* infos, void* stream);
+
+void gir_free(gir_handle* h);
+const char* gir_status_string(gir_status s);
+int64_t gir_handle_n(const gir_handle* h);
+
+/* ----- single steps of the hot path, exposed for parity testing and benchmarking ----- */
+
+/* Line 4 of Algorithm 4: r = b - A x in precision prec (GIR_FP64 or GIR_DD), rounded to FP64.
+ * All device pointers; r must not alias x or b. */
+gir_status gir_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
+                        double* r, gir_prec prec, void* stream);
+
+/* w = A v (trans = 0) or w = A^T v (trans = 1) in FP64 arithmetic (device pointers). */
+gir_status gir_gemv(const double* A, int64_t n, int64_t lda, const double* v, double* w,
+                    int trans, void* stream);
+
+/* Copy the factors out of a handle. LU: device n x n row-major float buffer receiving the
+ * u_f values of L (strictly lower, unit diagonal implied) and U (upper, incl. diagonal);
+ * ipiv: device int[n], rows k and ipiv[k] were interchanged at step k (0-based);
+ * R, S: device double[n] scalings; mu: host double. Any pointer may be NULL. */
+gir_status gir_export_factors(const gir_handle* h, float* LU, int32_t* ipiv, double* R, double* S,
+                              double* mu, void* stream);
+
+/* w = M^-1 v (trans = 0) or w = M^-T v (trans = 1), M^-1 = mu S U^-1 L^-1 P R (device pointers). */
+gir_status gir_apply_minv(gir_handle* h, const double* v, double* w, int trans, void* stream);
+
+/* w = M^-1 A v (trans = 0) or M^-T A^T v (trans = 1): one application of the preconditioned
+ * operator of Algorithm 4, line 5 (device pointers). */
+gir_status gir_apply_atilde(gir_handle* h, const double* A, int64_t lda, const double* v, double* w,
+                            int trans, void* stream);
+
+/* Algorithm 3 alone: d = GCRO-DR(m, k) solution of A~ d = c from d0 = 0, using and updating
+ * the handle's recycle space (forward operator). its_out (host, may be NULL) receives the
+ * number of Arnoldi steps; returns GIR_NOT_CONVERGED if max_its was reached. */
+gir_status gir_gcrodr(gir_handle* h, const double* A, int64_t lda, const double* c, double* d,
+                      int* its_out, void* stream);
+
+/* Copy the recycle space out: U, C device n x kcap column-major (column stride n); returns
+ * the current recycle dimension in *k_out (host). Forward (adjoint = 0) or adjoint space. */
+gir_status gir_export_recycle(const gir_handle* h, int adjoint, double* U, double* C, int kcap,
+                              int* k_out, void* stream);
+
+/* Drop the recycle spaces held by the handle (the next solve starts with a GMRES cycle). */
+gir_status gir_reset_recycle(gir_handle* h);
+
+/* Eigenvalues and selected real eigenbasis of a small dense matrix by the single-block FP64
+ * solver used for the harmonic Ritz step (Algorithm 3, lines 9 and 19). M: host d x d
+ * column-major (d <= GIR_MAX_M + GIR_MAX_K); wr, wi: host double[d] eigenvalues; P: host
+ * d x kcap column-major receiving a real basis of the eigenvectors of the k eigenvalues of
+ * largest (largest != 0) or smallest (largest == 0) magnitude with the conjugate-pair rule;
+ * *k_out receives the number of columns written. Runs on the GPU; for testing. */
+gir_status gir_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi,
+                         double* P, int kcap, int* k_out);
+
+/* GEPP of one panel (Algorithm 4, line 1, the column-by-column pivot search): factor the
+ * m x w FP32 block W (device, row-major, leading dimension ldw, w <= 32) in place with
+ * partial pivoting in FP32 arithmetic; ipiv (device int[w]) receives the 0-based pivot rows.
+ * cluster > 0 forces the number of cooperating CTAs (1..16), 0 chooses it from m.
+ * Returns GIR_SINGULAR on a zero pivot. For testing the panel kernel in isolation. */
+gir_status gir_lu_panel(float* W, int64_t ldw, int64_t m, int w, int32_t* ipiv, int cluster, void* stream);
+
+/* Trailing update of the factorization: C -= A B with A (M x K, leading dimension lda) and
+ * Bt = B^T (N x K, leading dimension ldbt) 16-bit u_f matrices (fmt GIR_BF16 or GIR_FP16,
+ * row-major, K contiguous), B itself (K x N, leading dimension ldb) for the CUDA-core path,
+ * C FP32 (M x N, ldc); exact products, FP32 accumulation. use_tc selects the tcgen05 tensor
+ * core path (1) or CUDA cores (0). All device pointers. For testing the update in isolation. */
+gir_status gir_lu_update(float* C, int64_t ldc, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                         const uint16_t* Bt, int64_t ldbt, int64_t M, int64_t N, int64_t K, gir_prec fmt,
+                         int use_tc, void* stream);
+
+/* Instrumentation (not in the paper). gir_trace_enable(1) records CUDA events on the
+ * launching stream around each phase of the factorization and of the solve (no added
+ * synchronisation); gir_trace_report writes "phase\tms\tcalls" lines into buf (host,
+ * buflen bytes, NUL-terminated), clears the totals and returns the full length needed.
+ * gir_launch_count returns the number of kernels this library has launched so far. */
+void gir_trace_enable(int on);
+int gir_trace_report(char* buf, int buflen);
+unsigned long long gir_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIR_H */

@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) recycled mixed-precision GMRES-IR for dense Ax = b.
+
+The solver (Algorithms 2-4 of Oktay & Carson, arXiv 2201.09827) is the CUDA library
+``libgir.so`` behind the C ABI in ``include/gir.h``; ``gir`` is its thin ctypes binding.
+"""
+from .gir import (  # noqa: F401
+    Params, Info, Factorization, GirSolve, GirError, residual, gemv, small_eig, batch_solve, load, lu_panel, lu_update, trace_enable, trace_report, launch_count,
+    library_path,
+)

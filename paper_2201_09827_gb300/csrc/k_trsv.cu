@@ -1,0 +1,336 @@
+// Application of the LU preconditioner M^-1 = mu S U^-1 L^-1 P R (Algorithm 4, line 5) and of
+// its transpose, on the u_f factors, with float-float arithmetic (about 48 significand bits).
+//
+// Triangular solves are blocked by b = 64 rows. One persistent CTA per block row takes a
+// ticket (atomic counter) in solve order; it streams the off-diagonal tiles of its block row
+// as the solution blocks it depends on are published (per-block ready flags carrying an
+// epoch number), then multiplies by the precomputed inverse of its diagonal block and
+// publishes its own block. A CTA only waits for tickets smaller than its own, which belong to
+// CTAs that are already running, so the scheme cannot deadlock; every wait is bounded and a
+// timeout sets an abort flag that releases all waiters.
+#include "gir_internal.cuh"
+#include "k_trsv.cuh"
+
+namespace gir {
+
+constexpr int TB = TRSV_BLOCK;  // 64
+
+// ------------------------------------------------------------------ diagonal-block inverses
+// D[I] = inv(T_II) for T = L (unit lower, upper == 0) or U (upper == 1), computed in FP64 from
+// the u_f values and stored as float-float (row-major b x b per block). Rows/columns beyond n
+// are padded with the identity.
+__global__ void __launch_bounds__(TB) k_diag_inv(const uint16_t* __restrict__ LU, int64_t ldl, int64_t n, int fmt,
+                                                 int upper, float2* __restrict__ D) {
+    extern __shared__ double dsm[];
+    double (*T)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(dsm);
+    double (*X)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(dsm + TB * (TB + 1));
+    const int I = blockIdx.x;
+    const int64_t base = (int64_t)I * TB;
+    const int c = threadIdx.x;
+    for (int i = 0; i < TB; ++i) {
+        int64_t gi = base + i, gc = base + c;
+        double v;
+        if (gi < n && gc < n) {
+            v = (double)uf_to_float(LU[gi * ldl + gc], fmt);
+            if (!upper) v = (c < i) ? v : (c == i ? 1.0 : 0.0);
+            else v = (c >= i) ? v : 0.0;
+        } else {
+            v = (i == c) ? 1.0 : 0.0;
+        }
+        T[i][c] = v;
+    }
+    __syncthreads();
+    // thread c solves T x = e_c
+    if (!upper) {
+        for (int i = 0; i < TB; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int q = 0; q < i; ++q) s = fma(-T[i][q], X[q][c], s);
+            X[i][c] = s;
+        }
+    } else {
+        for (int i = TB - 1; i >= 0; --i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int q = i + 1; q < TB; ++q) s = fma(-T[i][q], X[q][c], s);
+            X[i][c] = s / T[i][i];
+        }
+    }
+    __syncthreads();
+    for (int i = 0; i < TB; ++i) {
+        double v = X[i][c];
+        float h = __double2float_rn(v);
+        float l = __double2float_rn(v - (double)h);
+        D[((int64_t)I * TB + i) * TB + c] = make_float2(h, l);
+    }
+}
+
+// ------------------------------------------------------------------ persistent block TRSV
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// LOWER: forward order (block I depends on J < I); otherwise backward (J > I).
+// TRANS: the tile of block (I, J) is the transpose of stored tile (J, I).
+// UNIT: diagonal of T is one (only affects the diagonal inverse, precomputed).
+// Input zin: FP64 (zin64) or float-float (zin_ff); output: float-float yout.
+template <bool LOWER, bool TRANS>
+__global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, int64_t ldl, int fmt,
+                                              const float2* __restrict__ D, int64_t n, int nblk,
+                                              const double* __restrict__ zin64, const float2* __restrict__ zin_ff,
+                                              float2* __restrict__ yout, int* __restrict__ ready,
+                                              unsigned long long* __restrict__ ticket_ctr, unsigned long long base,
+                                              int epoch, int* __restrict__ abort_flag, int* __restrict__ flags) {
+    __shared__ float acc_h[TB], acc_l[TB];
+    __shared__ float yj_h[TB], yj_l[TB];
+    __shared__ float red_h[4][TB], red_l[4][TB];
+    __shared__ int s_ticket, s_abort;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) s_ticket = (int)(atomicAdd(ticket_ctr, 1ULL) - base);
+    __syncthreads();
+    const int t = s_ticket;
+    if (t < 0 || t >= nblk) {
+        // ticket counter out of step with the host (a failed earlier launch): give up loudly
+        if (tid == 0) { atomicOr(flags, DEV_TIMEOUT); atomicExch(abort_flag, 1); }
+        return;
+    }
+    const int I = LOWER ? t : (nblk - 1 - t);
+    const int64_t r0 = (int64_t)I * TB;
+
+    if (tid < TB) {
+        int64_t gi = r0 + tid;
+        float h = 0.0f, l = 0.0f;
+        if (gi < n) {
+            if (zin64) {
+                double v = zin64[gi];
+                h = __double2float_rn(v);
+                l = __double2float_rn(v - (double)h);
+            } else {
+                float2 v = zin_ff[gi];
+                h = v.x;
+                l = v.y;
+            }
+        }
+        acc_h[tid] = h;
+        acc_l[tid] = l;
+    }
+    if (tid == 0) s_abort = 0;
+    __syncthreads();
+
+    // thread mapping for a tile: !TRANS -> row r = tid / 4, column quarter q = tid % 4
+    //                            TRANS  -> row r = tid % 64, stored-row quarter q = tid / 64
+    const int r = TRANS ? (tid & 63) : (tid >> 2);
+    const int q = TRANS ? (tid >> 6) : (tid & 3);
+
+    for (int step = 0; step < nblk - 1; ++step) {
+        int J;
+        if (LOWER) { J = step; if (J >= I) break; }
+        else { J = nblk - 1 - step; if (J <= I) break; }
+        if (tid == 0) {
+            long long spins = 0;
+            while (ld_acquire(ready + J) != epoch) {
+                if (ld_acquire(abort_flag)) { s_abort = 1; break; }
+                if (++spins > SPIN_LIMIT) {
+                    atomicOr(flags, DEV_TIMEOUT);
+                    atomicExch(abort_flag, 1);
+                    s_abort = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const int64_t c0 = (int64_t)J * TB;
+        if (tid < TB) {
+            int64_t gc = c0 + tid;
+            float2 v = (gc < n) ? __ldcg(yout + gc) : make_float2(0.0f, 0.0f);
+            yj_h[tid] = v.x;
+            yj_l[tid] = v.y;
+        }
+        __syncthreads();
+        float sh = 0.0f, sl = 0.0f;
+        if (!TRANS) {
+            const int64_t gi = r0 + r;
+            if (gi < n) {
+                const uint16_t* row = LU + gi * ldl + c0 + q * 16;
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) {
+                    int c = q * 16 + cc;
+                    if (c0 + c < n) ff_acc_prod1(sh, sl, uf_to_float(row[cc], fmt), yj_h[c], yj_l[c]);
+                }
+            }
+        } else {
+            // element (r, c) of the block-(I,J) tile is stored at LU[(c0 + c), (r0 + r)]
+            const int64_t gcol = r0 + r;
+            if (gcol < n) {
+#pragma unroll 4
+                for (int cc = 0; cc < 16; ++cc) {
+                    int c = q * 16 + cc;
+                    int64_t grow = c0 + c;
+                    if (grow < n) ff_acc_prod1(sh, sl, uf_to_float(LU[grow * ldl + gcol], fmt), yj_h[c], yj_l[c]);
+                }
+            }
+        }
+        red_h[q][r] = sh;
+        red_l[q][r] = sl;
+        __syncthreads();
+        if (tid < TB) {
+            float h = red_h[0][tid], l = red_l[0][tid];
+            ff_acc_add(h, l, red_h[1][tid], red_l[1][tid]);
+            ff_acc_add(h, l, red_h[2][tid], red_l[2][tid]);
+            ff_acc_add(h, l, red_h[3][tid], red_l[3][tid]);
+            float ah = acc_h[tid], al = acc_l[tid];
+            ff_acc_add(ah, al, -h, -l);
+            ff ns = ff_norm(ah, al);
+            acc_h[tid] = ns.h;
+            acc_l[tid] = ns.l;
+        }
+        __syncthreads();
+    }
+
+    // y_I = D_I acc (TRANS: D_I^T acc); D is the inverse of the stored diagonal block.
+    {
+        float sh = 0.0f, sl = 0.0f;
+        const float2* Dblk = D + (int64_t)I * TB * TB;
+        if (!TRANS) {
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+                int c = q * 16 + cc;
+                float2 d = Dblk[r * TB + c];
+                ff_acc_prod2(sh, sl, d.x, d.y, acc_h[c], acc_l[c]);
+            }
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+                int c = q * 16 + cc;
+                float2 d = Dblk[c * TB + r];
+                ff_acc_prod2(sh, sl, d.x, d.y, acc_h[c], acc_l[c]);
+            }
+        }
+        red_h[q][r] = sh;
+        red_l[q][r] = sl;
+        __syncthreads();
+        if (tid < TB) {
+            float h = red_h[0][tid], l = red_l[0][tid];
+            ff_acc_add(h, l, red_h[1][tid], red_l[1][tid]);
+            ff_acc_add(h, l, red_h[2][tid], red_l[2][tid]);
+            ff_acc_add(h, l, red_h[3][tid], red_l[3][tid]);
+            ff ns = ff_norm(h, l);
+            int64_t gi = r0 + tid;
+            if (gi < n) yout[gi] = make_float2(ns.h, ns.l);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        st_release(ready + I, epoch);
+    }
+}
+
+// ------------------------------------------------------------------ pre/post scaling
+// forward: z[i] = R[p] * w[p], p = perm[i]          (P R w)
+__global__ void k_minv_pre(const double* __restrict__ w, const int* __restrict__ perm, const double* __restrict__ R,
+                           int64_t n, double* __restrict__ z) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = perm[i];
+        z[i] = R ? R[p] * w[p] : w[p];
+    }
+}
+// transpose: z = S w
+__global__ void k_minv_pre_t(const double* __restrict__ w, const double* __restrict__ S, int64_t n,
+                             double* __restrict__ z) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = S ? S[i] * w[i] : w[i];
+}
+// forward: out[i] = fl_u(mu S[i] y[i])
+__global__ void k_minv_post(const float2* __restrict__ y, const double* __restrict__ S, double mu, int64_t n,
+                            int round32, double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)y[i].x + (double)y[i].y;
+        if (S) v *= S[i] * mu;
+        if (round32) v = (double)__double2float_rn(v);
+        out[i] = v;
+    }
+}
+// transpose: out[perm[i]] = fl_u(mu R[perm[i]] y[i])
+__global__ void k_minv_post_t(const float2* __restrict__ y, const int* __restrict__ perm, const double* __restrict__ R,
+                              double mu, int64_t n, int round32, double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = perm[i];
+        double v = (double)y[i].x + (double)y[i].y;
+        if (R) v *= R[p] * mu;
+        if (round32) v = (double)__double2float_rn(v);
+        out[p] = v;
+    }
+}
+
+__global__ void k_ipiv_to_perm(const int* __restrict__ ipiv, int64_t n, int* __restrict__ perm) {
+    // single thread: sequential interchanges applied to the identity
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
+    for (int64_t k = 0; k < n; ++k) {
+        int p = ipiv[k];
+        if (p != k) {
+            int a = perm[k];
+            perm[k] = perm[p];
+            perm[p] = a;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, const int* ipiv,
+                      cudaStream_t s) {
+    st.n = n;
+    st.nblk = (int)((n + TB - 1) / TB);
+    st.fmt = fmt;
+    st.LU = LU;
+    st.ldl = ldl;
+    const int smem = 2 * TB * (TB + 1) * (int)sizeof(double);
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    count_launch(), k_diag_inv<<<st.nblk, TB, smem, s>>>(LU, ldl, n, fmt, 0, st.DL);
+    count_launch(), k_diag_inv<<<st.nblk, TB, smem, s>>>(LU, ldl, n, fmt, 1, st.DU);
+    count_launch(), k_ipiv_to_perm<<<1, 32, 0, s>>>(ipiv, n, st.perm);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+template <bool LOWER, bool TRANS>
+static gir_status run_trsv(TrsvState& st, const float2* D, const double* z64, const float2* zff, float2* y,
+                           int* flags, cudaStream_t s) {
+    int* ready = st.ready;
+    unsigned long long base = st.tickets;
+    st.tickets += (unsigned long long)st.nblk;
+    int epoch = ++st.epoch;
+    count_launch(), k_trsv<LOWER, TRANS><<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, st.nblk, z64, zff, y, ready,
+                                                 st.ticket_ctr, base, epoch, st.abort_flag, flags);
+    st.calls++;
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+gir_status apply_minv(TrsvState& st, const double* w, double* out, const double* R, const double* S, double mu,
+                      int trans, int round32, int* flags, cudaStream_t s) {
+    const int64_t n = st.n;
+    const int g = (int)gmin<int64_t>((n + 255) / 256, 1024);
+    if (!trans) {
+        count_launch(), k_minv_pre<<<g, 256, 0, s>>>(w, st.perm, R, n, st.z);
+        GIR_TRY((run_trsv<true, false>(st, st.DL, st.z, nullptr, st.y1, flags, s)));
+        GIR_TRY((run_trsv<false, false>(st, st.DU, nullptr, st.y1, st.y2, flags, s)));
+        count_launch(), k_minv_post<<<g, 256, 0, s>>>(st.y2, S, mu, n, round32, out);
+    } else {
+        count_launch(), k_minv_pre_t<<<g, 256, 0, s>>>(w, S, n, st.z);
+        // M^-T = mu R P^T L^-T U^-T S: first U^T (lower), then L^T (upper, unit)
+        GIR_TRY((run_trsv<true, true>(st, st.DU, st.z, nullptr, st.y1, flags, s)));
+        GIR_TRY((run_trsv<false, true>(st, st.DL, nullptr, st.y1, st.y2, flags, s)));
+        count_launch(), k_minv_post_t<<<g, 256, 0, s>>>(st.y2, st.perm, R, mu, n, round32, out);
+    }
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+}  // namespace gir

@@ -1,0 +1,348 @@
+// Bandwidth-bound kernels of the solve path: residual (Algorithm 4, line 4), the FP64
+// matrix-vector products inside A~ (line 5), and the tall-skinny products of GCRO-DR
+// (Algorithm 3: projections against [C_k V], solution/residual/recycle updates).
+//
+// Layouts: A is FP64 row-major with leading dimension lda; the Krylov/recycle bases are
+// column-major n x p blocks (column stride ldx), so every column is a contiguous vector.
+#include "gir_internal.cuh"
+
+namespace gir {
+
+// ------------------------------------------------------------------ row dot products
+// MODE 0: w_i = sum_j a_ij v_j            (FP64 FMA)
+// MODE 1: r_i = b_i - sum_j a_ij x_j      (FP64 FMA)
+// MODE 2: r_i = b_i - sum_j a_ij x_j      (double-double: exact FMA products, TwoSum accumulation)
+// One warp per row, 16-byte loads along the row when the row start is 16-byte aligned.
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, int64_t n, int64_t lda,
+                                                const double* __restrict__ x, const double* __restrict__ b,
+                                                double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps_total) {
+        const double* row = A + i * lda;
+        double sh = 0.0, sl = 0.0;
+        if (VEC) {
+            const double2* row2 = reinterpret_cast<const double2*>(row);
+            const double2* x2 = reinterpret_cast<const double2*>(x);
+            int64_t n2 = n >> 1;
+#pragma unroll 4
+            for (int64_t j = lane; j < n2; j += 32) {
+                double2 a = __ldcs(row2 + j);
+                double2 v = __ldg(x2 + j);
+                if (MODE == 2) {
+                    double p = a.x * v.x, e = fma(a.x, v.x, -p);
+                    double s = sh + p, bb = s - sh, t = (sh - (s - bb)) + (p - bb);
+                    sh = s; sl += t + e;
+                    p = a.y * v.y; e = fma(a.y, v.y, -p);
+                    s = sh + p; bb = s - sh; t = (sh - (s - bb)) + (p - bb);
+                    sh = s; sl += t + e;
+                } else {
+                    sh = fma(a.x, v.x, sh);
+                    sl = fma(a.y, v.y, sl);
+                }
+            }
+            if ((n & 1) && lane == 0) {
+                double a = row[n - 1], v = x[n - 1];
+                if (MODE == 2) {
+                    double p = a * v, e = fma(a, v, -p);
+                    double s = sh + p, bb = s - sh, t = (sh - (s - bb)) + (p - bb);
+                    sh = s; sl += t + e;
+                } else {
+                    sh = fma(a, v, sh);
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int64_t j = lane; j < n; j += 32) {
+                double a = __ldcs(row + j), v = __ldg(x + j);
+                if (MODE == 2) {
+                    double p = a * v, e = fma(a, v, -p);
+                    double s = sh + p, bb = s - sh, t = (sh - (s - bb)) + (p - bb);
+                    sh = s; sl += t + e;
+                } else {
+                    sh = fma(a, v, sh);
+                }
+            }
+        }
+        if (MODE != 2) {
+            double s = warp_sum(sh + sl);
+            if (lane == 0) out[i] = (MODE == 0) ? s : (b[i] - s);
+        } else {
+            // double-double butterfly reduction of (sh, sl)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double oh = __shfl_xor_sync(0xffffffffu, sh, o);
+                double ol = __shfl_xor_sync(0xffffffffu, sl, o);
+                double s = sh + oh, bb = s - sh, t = (sh - (s - bb)) + (oh - bb);
+                t += sl + ol;
+                sh = s + t;
+                sl = t - (sh - s);
+            }
+            if (lane == 0) {
+                // r = b - (sh + sl), in double-double then rounded
+                double bi = b[i];
+                double s = bi - sh, bb = s - bi, t = (bi - (s - bb)) + (-sh - bb);
+                t -= sl;
+                out[i] = s + t;
+            }
+        }
+    }
+}
+
+static int grid_for_rows(int64_t n) {
+    int64_t g = (n + 7) / 8;  // 8 warps per block
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+static bool aligned16(const void* p, int64_t ld) {
+    return ((uintptr_t)p % 16 == 0) && (ld % 2 == 0);
+}
+
+gir_status launch_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
+                           double* r, int dd, cudaStream_t s) {
+    if (n <= 0) return GIR_OK;
+    int g = grid_for_rows(n);
+    bool v = aligned16(A, lda) && ((uintptr_t)x % 16 == 0);
+    if (dd) {
+        if (v) count_launch(), k_rowdot<2, true><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
+        else count_launch(), k_rowdot<2, false><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
+    } else {
+        if (v) count_launch(), k_rowdot<1, true><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
+        else count_launch(), k_rowdot<1, false><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
+    }
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+// ------------------------------------------------------------------ A^T v
+// Block (row chunk rc, column chunk cc): partial[rc][j] = sum_{i in rc} a_ij v_i.
+constexpr int GT_ROWS = 256;
+constexpr int GT_COLS = 512;  // 256 threads x 2 columns
+
+__global__ void __launch_bounds__(256) k_gemv_t_partial(const double* __restrict__ A, int64_t n, int64_t lda,
+                                                        const double* __restrict__ v, double* __restrict__ part) {
+    const int64_t i0 = (int64_t)blockIdx.y * GT_ROWS;
+    const int64_t j = (int64_t)blockIdx.x * GT_COLS + threadIdx.x * 2;
+    const int64_t i1 = min(n, i0 + GT_ROWS);
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+        double vi = __ldg(v + i);
+        const double* row = A + i * lda;
+        if (j < n) a0 = fma(__ldcs(row + j), vi, a0);
+        if (j + 1 < n) a1 = fma(__ldcs(row + j + 1), vi, a1);
+    }
+    double* p = part + (int64_t)blockIdx.y * n;
+    if (j < n) p[j] = a0;
+    if (j + 1 < n) p[j + 1] = a1;
+}
+
+__global__ void k_sum_rows(const double* __restrict__ part, int nparts, int64_t n, double* __restrict__ out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < nparts; ++q) s += part[(int64_t)q * n + j];
+        out[j] = s;
+    }
+}
+
+gir_status launch_gemv(const double* A, int64_t n, int64_t lda, const double* v, double* w, int trans,
+                       double* scratch, cudaStream_t s) {
+    if (n <= 0) return GIR_OK;
+    if (!trans) {
+        int g = grid_for_rows(n);
+        if (aligned16(A, lda) && ((uintptr_t)v % 16 == 0)) count_launch(), k_rowdot<0, true><<<g, 256, 0, s>>>(A, n, lda, v, nullptr, w);
+        else count_launch(), k_rowdot<0, false><<<g, 256, 0, s>>>(A, n, lda, v, nullptr, w);
+    } else {
+        dim3 grid((unsigned)((n + GT_COLS - 1) / GT_COLS), (unsigned)((n + GT_ROWS - 1) / GT_ROWS));
+        count_launch(), k_gemv_t_partial<<<grid, 256, 0, s>>>(A, n, lda, v, scratch);
+        count_launch(), k_sum_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, (int)grid.y, n, w);
+    }
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+// ------------------------------------------------------------------ tall-skinny X^T Y
+// G[c + t*p] = sum_i X[i, c] Y[i, t]; block = row chunk of TS_CHUNK rows, one warp per (c, t) pair.
+constexpr int TS_CHUNK = 1024;
+
+__global__ void __launch_bounds__(256) k_gemm_tn_partial(const double* __restrict__ X, int64_t ldx, int p,
+                                                         const double* __restrict__ Y, int64_t ldy, int q,
+                                                         int64_t n, double* __restrict__ part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * TS_CHUNK;
+    const int64_t i1 = min(n, i0 + TS_CHUNK);
+    const int pairs = p * q;
+    for (int pq = warp; pq < pairs; pq += 8) {
+        int c = pq % p, t = pq / p;
+        const double* xc = X + (int64_t)c * ldx;
+        const double* yt = Y + (int64_t)t * ldy;
+        double acc = 0.0;
+        for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(xc[i], yt[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) part[(int64_t)blockIdx.x * pairs + pq] = acc;
+    }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nparts, int p, int cnt, int ldg,
+                            double* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < nparts; ++q) s += part[(int64_t)q * cnt + e];
+        out[(e % p) + (int64_t)(e / p) * ldg] = s;
+    }
+}
+
+gir_status launch_gemm_tn(const double* X, int64_t ldx, int p, const double* Y, int64_t ldy, int q, int64_t n,
+                          double* G, int ldg, double* scratch, cudaStream_t s) {
+    if (p <= 0 || q <= 0) return GIR_OK;
+    int nb = (int)((n + TS_CHUNK - 1) / TS_CHUNK);
+    if (nb < 1) nb = 1;
+    count_launch(), k_gemm_tn_partial<<<nb, 256, 0, s>>>(X, ldx, p, Y, ldy, q, n, scratch);
+    int cnt = p * q;
+    count_launch(), k_sum_parts<<<(cnt + 127) / 128, 128, 0, s>>>(scratch, nb, p, cnt, ldg, G);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+gir_status launch_multidot(const double* X, int64_t ldx, int ncols, const double* y, int64_t n, double* out,
+                           double* scratch, cudaStream_t s) {
+    return launch_gemm_tn(X, ldx, ncols, y, n, 1, n, out, ncols, scratch, s);
+}
+
+// ------------------------------------------------------------------ Y = beta Y + X Cf
+// Thread per row; coefficients staged in shared memory; outputs in groups of 8 columns.
+__global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, int64_t ldx, int p,
+                                                 const double* __restrict__ Cf, int ldc, int q,
+                                                 double* __restrict__ Y, int64_t ldy, double alpha, double beta,
+                                                 int64_t n, int round32) {
+    extern __shared__ double sc[];
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+        int c = e % p, t = e / p;
+        sc[e] = Cf[c + (int64_t)t * ldc];
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int t0 = 0; t0 < q; t0 += 8) {
+            double acc[8];
+#pragma unroll
+            for (int tt = 0; tt < 8; ++tt) acc[tt] = 0.0;
+            for (int c = 0; c < p; ++c) {
+                double xv = X[i + (int64_t)c * ldx];
+#pragma unroll
+                for (int tt = 0; tt < 8; ++tt)
+                    if (t0 + tt < q) acc[tt] = fma(xv, sc[c + (t0 + tt) * p], acc[tt]);
+            }
+#pragma unroll
+            for (int tt = 0; tt < 8; ++tt) {
+                if (t0 + tt < q) {
+                    double* y = Y + i + (int64_t)(t0 + tt) * ldy;
+                    double v = (beta == 0.0) ? alpha * acc[tt] : fma(beta, *y, alpha * acc[tt]);
+                    if (round32) v = (double)__double2float_rn(v);
+                    *y = v;
+                }
+            }
+        }
+    }
+}
+
+gir_status launch_gemm_nn(const double* X, int64_t ldx, int p, const double* Cf, int ldc, int q, double* Y,
+                          int64_t ldy, double alpha, double beta, int64_t n, int round32, cudaStream_t s) {
+    if (q <= 0 || n <= 0) return GIR_OK;
+    if (p <= 0) {
+        // Y = beta Y
+        if (beta == 0.0) {
+            for (int t = 0; t < q; ++t) GIR_CUDA_TRY(cudaMemsetAsync(Y + (int64_t)t * ldy, 0, n * sizeof(double), s));
+            return GIR_OK;
+        }
+        if (beta == 1.0) return GIR_OK;
+    }
+    size_t smem = (size_t)p * q * sizeof(double);
+    if (smem > 48 * 1024) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        if (smem > 200 * 1024) return GIR_INVALID_ARG;
+    }
+    int g = (int)gmin<int64_t>((n + 255) / 256, 152 * 8);
+    count_launch(), k_gemm_nn<<<g, 256, smem, s>>>(X, ldx, p, Cf, ldc, q, Y, ldy, alpha, beta, n, round32);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+// ------------------------------------------------------------------ norms
+__global__ void __launch_bounds__(256) k_sumsq_partial(const double* __restrict__ x, int64_t n,
+                                                       double* __restrict__ part) {
+    __shared__ double sw[8];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(x[i], x[i], acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < 8 ? sw[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_finish_norm2(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += 32) acc += part[q];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) *out = sqrt(acc);
+}
+
+gir_status launch_norm2(const double* x, int64_t n, double* out, double* scratch, cudaStream_t s) {
+    int g = (int)gmin<int64_t>((n + 255) / 256, 256);
+    if (g < 1) g = 1;
+    count_launch(), k_sumsq_partial<<<g, 256, 0, s>>>(x, n, scratch);
+    count_launch(), k_finish_norm2<<<1, 32, 0, s>>>(scratch, g, out);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+__global__ void __launch_bounds__(256) k_absmax(const double* __restrict__ x, int64_t n, unsigned long long* out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = fabs(x[i]);
+        if (!(v <= m)) m = v;  // propagates NaN
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+gir_status launch_norminf(const double* x, int64_t n, double* out, cudaStream_t s) {
+    GIR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), s));
+    int g = (int)gmin<int64_t>((n + 255) / 256, 256);
+    if (g < 1) g = 1;
+    count_launch(), k_absmax<<<g, 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+// ||A||_inf = max_i sum_j |a_ij|: one warp per row.
+__global__ void __launch_bounds__(256) k_rowabs(const double* __restrict__ A, int64_t n, int64_t lda,
+                                                double* __restrict__ rs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps_total) {
+        double acc = 0.0;
+        for (int64_t j = lane; j < n; j += 32) acc += fabs(A[i * lda + j]);
+        acc = warp_sum(acc);
+        if (lane == 0) rs[i] = acc;
+    }
+}
+
+gir_status launch_matrix_norminf(const double* A, int64_t n, int64_t lda, double* out, double* scratch,
+                                 cudaStream_t s) {
+    count_launch(), k_rowabs<<<grid_for_rows(n), 256, 0, s>>>(A, n, lda, scratch);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return launch_norminf(scratch, n, out, s);
+}
+
+}  // namespace gir

@@ -1,0 +1,117 @@
+// Kernel launch counter and optional phase timing shared by all translation units.
+//
+// Timing records a pair of CUDA events on the launching stream around each phase without
+// synchronising; elapsed times are resolved and summed per phase name when the report is
+// requested (or when the event pool fills up).
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gir_internal.cuh"
+#include "trace.cuh"
+
+namespace gir {
+
+static unsigned long long g_launches = 0;
+void count_launch() { ++g_launches; }
+unsigned long long launch_count() { return g_launches; }
+
+namespace {
+struct Slot {
+    const char* name;
+    cudaEvent_t a, b;
+};
+struct Agg {
+    const char* name;
+    double ms;
+    long long cnt;
+};
+struct TraceState {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Slot> slots;
+    std::vector<Agg> agg;
+    size_t used = 0;
+    void resolve() {
+        if (slots.empty()) return;
+        cudaDeviceSynchronize();
+        for (auto& s : slots) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, s.a, s.b) != cudaSuccess) continue;
+            bool found = false;
+            for (auto& g : agg)
+                if (std::strcmp(g.name, s.name) == 0) {
+                    g.ms += t;
+                    g.cnt += 1;
+                    found = true;
+                    break;
+                }
+            if (!found) agg.push_back({s.name, (double)t, 1});
+        }
+        slots.clear();
+        used = 0;
+    }
+    cudaEvent_t next() {
+        if (used >= pool.size()) {
+            if (pool.size() >= 16384) resolve();
+            if (used >= pool.size()) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                pool.push_back(e);
+            }
+        }
+        return pool[used++];
+    }
+};
+TraceState g_trace;
+}  // namespace
+
+bool trace_on() { return g_trace.on; }
+
+int trace_begin(cudaStream_t s) {
+    if (!g_trace.on) return -1;
+    cudaEvent_t a = g_trace.next();
+    cudaEventRecord(a, s);
+    g_trace.slots.push_back({nullptr, a, nullptr});
+    return (int)g_trace.slots.size() - 1;
+}
+
+void trace_end(int slot, const char* name, cudaStream_t s) {
+    if (!g_trace.on || slot < 0 || slot >= (int)g_trace.slots.size()) return;
+    cudaEvent_t b = g_trace.next();
+    cudaEventRecord(b, s);
+    g_trace.slots[slot].name = name;
+    g_trace.slots[slot].b = b;
+}
+
+}  // namespace gir
+
+extern "C" {
+
+void gir_trace_enable(int on) {
+    gir::g_trace.resolve();
+    gir::g_trace.agg.clear();
+    gir::g_trace.on = on != 0;
+}
+
+int gir_trace_report(char* buf, int buflen) {
+    gir::g_trace.resolve();
+    std::string out;
+    char line[256];
+    for (auto& g : gir::g_trace.agg) {
+        snprintf(line, sizeof(line), "%s\t%.6f\t%lld\n", g.name, g.ms, g.cnt);
+        out += line;
+    }
+    gir::g_trace.agg.clear();
+    if (buf && buflen > 0) {
+        int n = (int)out.size() < buflen - 1 ? (int)out.size() : buflen - 1;
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int)out.size();
+}
+
+unsigned long long gir_launch_count(void) { return gir::g_launches; }
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Phase timing hooks (trace.cu). Off unless gir_trace_enable(1) or GIR_TRACE=1.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gir {
+bool trace_on();
+int trace_begin(cudaStream_t s);
+void trace_end(int slot, const char* name, cudaStream_t s);
+}  // namespace gir

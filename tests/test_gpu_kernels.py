@@ -1,0 +1,199 @@
+"""GPU parity of the single steps of the hot path against the CPU oracle (through the C ABI)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dd as odd
+from oracle import lu as olu
+from oracle.formats import round_to, UNIT_ROUNDOFF
+from synth import randsvd, prolate
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2201_09827_gb300 import gir
+    gir.load()
+    return gir
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [1, 7, 128, 129, 1000, 1023])
+def test_residual_fp64_and_dd(G, n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    x = rng.standard_normal(n)
+    b = A @ x + 1e-12 * rng.standard_normal(n)        # heavy cancellation
+    rh, rl = odd.dd_residual(A, x, b)
+    exact = rh + rl
+    scale = np.abs(A) @ np.abs(x) + np.abs(b)
+    r64 = G.residual(cuda(A), cuda(x), cuda(b), "fp64").cpu().numpy()
+    assert np.all(np.abs(r64 - exact) <= 1.01 * n * U64 * scale + 1e-300)
+    rdd = G.residual(cuda(A), cuda(x), cuda(b), "dd").cpu().numpy()
+    assert np.all(np.abs(rdd - exact) <= U64 * np.abs(exact) + 4 * n * 2.0 ** -106 * scale + 1e-300)
+
+
+def test_residual_strided(G):
+    n, lda = 300, 333
+    rng = np.random.default_rng(5)
+    Afull = rng.standard_normal((n, lda))
+    A = Afull[:, :n]
+    x = rng.standard_normal(n)
+    b = rng.standard_normal(n)
+    Ad = cuda(Afull)[:, :n]
+    r = G.residual(Ad, cuda(x), cuda(b), "dd").cpu().numpy()
+    rh, rl = odd.dd_residual(A, x, b)
+    assert np.abs(r - (rh + rl)).max() <= 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 33, 512, 1000])
+@pytest.mark.parametrize("trans", [False, True])
+def test_gemv(G, n, trans):
+    rng = np.random.default_rng(n + trans)
+    A = rng.standard_normal((n, n))
+    v = rng.standard_normal(n)
+    w = G.gemv(cuda(A), cuda(v), trans=trans).cpu().numpy()
+    ref = (A.T if trans else A) @ v
+    assert np.abs(w - ref).max() <= 2 * n * U64 * (np.abs(A).max() * np.abs(v).sum() + 1)
+
+
+def panel_oracle(W):
+    """GEPP of an FP32 panel with correctly rounded FP32 quotients and fused updates."""
+    W = W.astype(np.float64).copy()
+    m, w = W.shape
+    piv = []
+    f32 = lambda z: round_to(z, "fp32")
+    for k in range(w):
+        p = k + int(np.argmax(np.abs(W[k:, k])))
+        piv.append(p)
+        W[[k, p]] = W[[p, k]]
+        l = f32(W[k + 1:, k] / W[k, k])
+        W[k + 1:, k] = l
+        W[k + 1:, k + 1:] = f32(W[k + 1:, k + 1:] - np.outer(l, W[k, k + 1:]))
+    return W, np.array(piv)
+
+
+@pytest.mark.parametrize("m,w,cluster", [(32, 32, 1), (200, 32, 1), (2000, 32, 2), (2000, 32, 5), (3001, 17, 13),
+                                         (1000, 16, 16), (77, 1, 3), (4096, 7, 8)])
+def test_panel_bitexact(G, m, w, cluster):
+    rng = np.random.default_rng(m * 31 + w)
+    W = rng.standard_normal((m, w)).astype(np.float32)
+    W[rng.integers(0, m, 5), 0] = 3.0        # exact ties in the first column: lowest row wins
+    Wd = cuda(W)
+    ipiv = G.lu_panel(Wd, cluster=cluster).cpu().numpy()
+    Wo, po = panel_oracle(W)
+    assert np.array_equal(ipiv, po)
+    assert np.array_equal(Wd.cpu().numpy().astype(np.float64), Wo)
+
+
+def test_panel_singular_column(G):
+    W = np.random.default_rng(1).standard_normal((100, 8)).astype(np.float32)
+    W[:, 3] = W[:, 1] * 2.0
+    W[:, 3] -= W[:, 1] * 2.0                 # exactly zero column
+    with pytest.raises(G.GirError) as e:
+        G.lu_panel(cuda(W))
+    assert e.value.status == G.GIR_SINGULAR
+
+
+@pytest.mark.parametrize("fmt,tdt", [("bf16", torch.bfloat16), ("fp16", torch.float16)])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 500, 256), (1000, 700, 32), (257, 129, 200), (4096, 2048, 512)])
+@pytest.mark.parametrize("tc", [True, False])
+def test_trailing_update(G, fmt, tdt, M, N, K, tc):
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(tdt)
+    B = torch.randn(K, N, device="cuda", generator=g).to(tdt)
+    C0 = torch.randn(M, N, device="cuda", dtype=torch.float32, generator=g)
+    ref = C0.double() - A.double() @ B.double()          # exact products, FP64 sums
+    Cm = C0.clone()
+    G.lu_update(Cm, A.view(torch.int16), B.view(torch.int16), fmt, use_tc=tc)
+    bound = (K + 2) * 2.0 ** -24 * ((A.double().abs() @ B.double().abs()) + C0.double().abs())
+    assert bool(((Cm.double() - ref).abs() <= bound).all())
+
+
+def _gpu_factors(G, A, fmt, m=20, k=5):
+    import paper_2201_09827_gb300 as pkg
+    F = pkg.Factorization(cuda(A), pkg.Params(uf=fmt, m=m, k=k))
+    LU, ipiv, R, S, mu = F.export_factors()
+    LU = LU.double().cpu().numpy()
+    n = A.shape[0]
+    ipiv = ipiv.cpu().numpy()
+    Fo = olu.Factors(n, fmt, np.tril(LU, -1) + np.eye(n), np.triu(LU), olu.ipiv_to_perm(ipiv), ipiv,
+                     R.cpu().numpy(), S.cpu().numpy(), mu)
+    return F, Fo
+
+
+@pytest.mark.parametrize("n,fmt", [(32, "bf16"), (20, "fp16")])
+def test_factor_single_panel_bitexact(G, n, fmt):
+    """n <= panel width: the factorization is one FP32 GEPP panel, identical to the oracle's model."""
+    A = randsvd(n, 1e3, seed=3)
+    F, Fg = _gpu_factors(G, A, fmt)
+    Fo = olu.lu_block(A, fmt, w=32)
+    assert np.array_equal(Fg.ipiv, Fo.ipiv)
+    assert np.array_equal(Fg.L, Fo.L) and np.array_equal(Fg.U, Fo.U)
+    assert np.array_equal(Fg.R, Fo.R) and np.array_equal(Fg.S, Fo.S) and Fg.mu == Fo.mu
+    F.close()
+
+
+@pytest.mark.parametrize("n,fmt", [(100, "bf16"), (300, "bf16"), (300, "fp16"), (1000, "fp16"), (1537, "bf16")])
+def test_factor_properties(G, n, fmt):
+    """Beyond one panel the FP32 summation order differs from the oracle, so the factors are
+    checked by what both must satisfy: partial pivoting and the u_f backward error bound."""
+    A = randsvd(n, 1e3, seed=n)
+    F, Fg = _gpu_factors(G, A, fmt)
+    Fo = olu.lu_block(A, fmt, w=32)
+    # identical input scaling (a plain definition: powers of two from row/column maxima)
+    assert np.array_equal(Fg.R, Fo.R) and np.array_equal(Fg.S, Fo.S) and Fg.mu == Fo.mu
+    As = Fg.mu * (A * Fg.R[:, None]) * Fg.S[None, :]
+    E = np.abs(As[Fg.perm] - Fg.L @ Fg.U).max() / (np.abs(Fg.L) @ np.abs(Fg.U)).max()
+    Eo = np.abs(As[Fo.perm] - Fo.L @ Fo.U).max() / (np.abs(Fo.L) @ np.abs(Fo.U)).max()
+    assert E <= 8 * UNIT_ROUNDOFF[fmt] and E <= 4 * Eo + UNIT_ROUNDOFF[fmt]
+    assert np.abs(np.tril(Fg.L, -1)).max() <= 1.0
+    # the stored values are representable in u_f
+    assert np.array_equal(round_to(Fg.U, fmt), Fg.U)
+    F.close()
+
+
+@pytest.mark.parametrize("n,fmt", [(64, "bf16"), (300, "fp16"), (1000, "bf16"), (1031, "fp16")])
+def test_apply_minv_and_atilde(G, n, fmt):
+    """With the same (GPU) factors, M^-1 v and M^-1 A v agree with the oracle's FP64 substitution
+    to the float-float accuracy of the triangular solves (about 2^-45 relative)."""
+    A = randsvd(n, 1e4, seed=7)
+    F, Fg = _gpu_factors(G, A, fmt)
+    rng = np.random.default_rng(8)
+    for trans in (False, True):
+        v = rng.standard_normal(n)
+        w = F.apply_minv(cuda(v), trans=trans).cpu().numpy()
+        wo = olu.apply_minv_t(Fg, v) if trans else olu.apply_minv(Fg, v)
+        assert np.abs(w - wo).max() <= 1e-11 * np.abs(wo).max()
+        w = F.apply_atilde(cuda(A), cuda(v), trans=trans).cpu().numpy()
+        wo = olu.apply_atilde_t(A, Fg, v) if trans else olu.apply_atilde(A, Fg, v)
+        assert np.abs(w - wo).max() <= 1e-11 * np.abs(wo).max()
+    F.close()
+
+
+@pytest.mark.parametrize("d", [1, 2, 5, 12, 30, 50, 112])
+@pytest.mark.parametrize("largest", [0, 1])
+def test_small_eig(G, d, largest):
+    rng = np.random.default_rng(d + 100 * largest)
+    M = rng.standard_normal((d, d))
+    k = min(10, max(1, d - 1))
+    wr, wi, P, failed = G.small_eig(M, k, largest, 200)
+    assert not failed
+    lam = np.linalg.eigvals(M)
+    got = np.sort_complex(wr + 1j * wi)
+    assert np.abs(got - np.sort_complex(lam)).max() <= 1e-10 * max(1.0, np.abs(lam).max())
+    # P spans an invariant subspace whose eigenvalues are the selected ones
+    T = np.linalg.lstsq(P, M @ P, rcond=None)[0]
+    assert np.linalg.norm(M @ P - P @ T) <= 1e-9 * max(1.0, np.linalg.norm(M @ P))
+    mags = np.sort(np.abs(np.linalg.eigvals(T)))
+    allm = np.sort(np.abs(lam))
+    want = allm[::-1][:P.shape[1]] if largest else allm[:P.shape[1]]
+    assert np.allclose(np.sort(mags), np.sort(want), rtol=1e-8, atol=1e-12)
+    assert abs(P.shape[1] - k) <= 1

@@ -1,0 +1,276 @@
+"""End-to-end GPU parity of RGMRES-IR with the CPU oracle, on the paper's workloads at sizes the
+oracle finishes in seconds, plus GCRO-DR invariants, the adjoint, batches and status paths.
+
+Tolerances (stated for a method whose inner iteration depends on rounding): final normwise
+backward error <= 4 x the oracle's (floored at the unit roundoff of u), total GMRES
+iterations within +-10% (+1), same convergence status, and the forward error within the
+Table 2 level for the precision triple."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.ir import Params as OP, solve as osolve, normwise_berr, forward_err, exact_solution
+from oracle import lu as olu
+from oracle import gcrodr as ogc
+from oracle.formats import UNIT_ROUNDOFF
+from synth import randsvd, prolate, convdiff, rhs_uniform, normal_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2201_09827_gb300 as p
+    p.load()
+    return p
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_both(pkg, A, b, uf, u, ur, m, k, tau, imax=10, target=None, max_its=None, carry=1):
+    prm = pkg.Params(uf=uf, u=u, ur=ur, m=m, k=k, tau=tau, imax=imax,
+                     target_berr=-1.0 if target is None else target, carry_mode=carry,
+                     max_its=max_its or 0)
+    F = pkg.Factorization(cuda(A), prm)
+    x, info = F.solve(cuda(A), cuda(b))
+    x = x.cpu().numpy()
+    F.close()
+    op = OP(uf=uf, u=u, ur=ur, ua="u" if u == "fp64" else "u2", m=m, k=k, tau=tau, imax=imax, target=target,
+            lu_w=32, max_its=max_its or 20 * m, carry_mode=carry)
+    xo, io, _, _ = osolve(A, b, op)
+    return x, info, xo, io
+
+
+def assert_parity(A, b, x, info, xo, io, u):
+    uu = UNIT_ROUNDOFF[u]
+    assert (info.status == 0) == io.converged, (info.status, io.status)
+    be, beo = normwise_berr(A, x, b), normwise_berr(A, xo, b)
+    if io.converged:
+        assert be <= 4 * max(beo, uu)
+        assert abs(info.total_its - io.total) <= 0.1 * io.total + 1, (info.its, io.its)
+        assert info.ir_steps == io.steps or abs(info.ir_steps - io.steps) <= 1
+
+
+@pytest.mark.parametrize("kappa,uf", [(1e2, "bf16"), (1e2, "fp16"), (1e4, "fp16")])
+def test_randsvd_fp64_working(pkg, kappa, uf):
+    """The headline triple (u_f, FP64, FP64) with tau = 1e-8 and target 1e-15, n = 1024."""
+    n = 1024
+    A = randsvd(n, kappa, seed=0)
+    b = A @ normal_vector(n, 2)
+    x, info, xo, io = run_both(pkg, A, b, uf, "fp64", "fp64", 50, 10, 1e-8, target=1e-15)
+    assert_parity(A, b, x, info, xo, io, "fp64")
+    assert normwise_berr(A, x, b) <= 1e-15
+
+
+@pytest.mark.parametrize("kappa,uf", [(1e2, "fp16"), (1e4, "fp16"), (1e2, "bf16")])
+def test_randsvd_fp32_working(pkg, kappa, uf):
+    """The precision sweep with FP32 working precision (u = FP32, u_r = FP64, tau = 1e-4):
+    backward error and forward error at the single-precision level of Table 2."""
+    n = 768
+    A = randsvd(n, kappa, seed=1)
+    xt = normal_vector(n, 2)
+    b = A @ xt
+    x, info, xo, io = run_both(pkg, A, b, uf, "fp32", "fp64", 50, 10, 1e-4)
+    assert_parity(A, b, x, info, xo, io, "fp32")
+    xs = exact_solution(A, b)
+    kinf = np.linalg.norm(A, np.inf) * np.linalg.norm(np.linalg.inv(A), np.inf)
+    assert forward_err(x, xs) <= 10 * (UNIT_ROUNDOFF["fp32"] + kinf * UNIT_ROUNDOFF["fp64"]) + 10 * forward_err(xo, xs)
+
+
+def test_small_config_paper_precisions(pkg):
+    """n = 200, kappa_2 = 1e6, (fp16, fp32, fp64), GCRO-DR(20, 5), tau = 1e-4: restarted
+    GCRO-DR stagnates on this matrix in both implementations (the paper's "-")."""
+    A = randsvd(200, 1e6, seed=0)
+    b = rhs_uniform(200, 0)
+    x, info, xo, io = run_both(pkg, A, b, "fp16", "fp32", "fp64", 20, 5, 1e-4, imax=10, max_its=400)
+    assert not io.converged and info.status == 1
+
+
+def test_small_config_converging_companion(pkg):
+    A = randsvd(200, 1e6, seed=0)
+    b = rhs_uniform(200, 0)
+    x, info, xo, io = run_both(pkg, A, b, "fp16", "fp32", "fp64", 100, 20, 1e-4, imax=10, max_its=2000)
+    assert_parity(A, b, x, info, xo, io, "fp32")
+
+
+@pytest.mark.parametrize("w,expect", [(0.25, False), (0.495, True)])
+def test_prolate_dd_residual(pkg, w, expect):
+    """Prolate Toeplitz with (bf16, fp64, double-double) and GCRO-DR(30, 10): w = 0.25 is
+    numerically singular (no convergence); a well-conditioned companion converges."""
+    n = 512
+    A = prolate(n, w)
+    b = rhs_uniform(n, 0)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "dd", 30, 10, 1e-8, imax=6, max_its=600)
+    assert io.converged == expect
+    assert_parity(A, b, x, info, xo, io, "fp64")
+
+
+def test_recycling_vs_no_recycling(pkg):
+    """Recycling across refinement steps: the second step needs fewer iterations with k > 0
+    on a prolate matrix whose preconditioned spectrum has outliers (Section 4.1)."""
+    A = prolate(400, 0.49)
+    b = rhs_uniform(400, 1)
+    res = {}
+    for k in (0, 8):
+        x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 30, k, 1e-8, imax=2, target=0.0)
+        assert info.its[0] == io.its[0] or abs(info.its[0] - io.its[0]) <= 1
+        res[k] = (info.its, io.its)
+    assert res[8][0][1] < res[0][0][1]           # GPU: recycling helps step 2
+    assert res[8][1][1] < res[0][1][1]           # oracle: same conclusion
+
+
+def test_convdiff(pkg):
+    A = convdiff(24, 50.0)
+    b = rhs_uniform(A.shape[0], 4)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 40, 10, 1e-8, target=1e-15)
+    assert_parity(A, b, x, info, xo, io, "fp64")
+
+
+def test_carry_literal_and_reuse_agree(pkg):
+    A = prolate(300, 0.485)
+    b = rhs_uniform(300, 1)
+    out = []
+    for carry in (0, 1):
+        x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 30, 8, 1e-8, target=1e-15, carry=carry)
+        assert_parity(A, b, x, info, xo, io, "fp64")
+        out.append(info)
+    assert abs(out[0].total_its - out[1].total_its) <= 2
+    assert out[0].carry_applies[1:] and all(c > 0 for c in out[0].carry_applies[1:])
+    assert all(c == 0 for c in out[1].carry_applies)
+
+
+def test_gcrodr_invariants(pkg):
+    """After each GCRO-DR solve the recycle space satisfies C^T C = I and A~ U = C (Section 2),
+    and d solves A~ d = c to the tolerance; the second solve recycles."""
+    n = 400
+    A = prolate(n, 0.49)
+    prm = pkg.Params(uf="bf16", m=30, k=8, tau=1e-10)
+    F = pkg.Factorization(cuda(A), prm)
+    LU, ipiv, R, S, mu = F.export_factors()
+    LU = LU.double().cpu().numpy()
+    ip = ipiv.cpu().numpy()
+    Fo = olu.Factors(n, "bf16", np.tril(LU, -1) + np.eye(n), np.triu(LU), olu.ipiv_to_perm(ip), ip,
+                     R.cpu().numpy(), S.cpu().numpy(), mu)
+    op = lambda v: olu.apply_atilde(A, Fo, v)
+    rng = np.random.default_rng(0)
+    Y = None
+    for step in range(2):
+        c = rng.standard_normal(n)
+        d, its, st = F.gcrodr(cuda(A), cuda(c))
+        assert st == 0
+        d = d.cpu().numpy()
+        assert np.linalg.norm(c - op(d)) <= 1.05e-10 * np.linalg.norm(c)
+        U, Cm = F.export_recycle()
+        U, Cm = U.cpu().numpy(), Cm.cpu().numpy()
+        kk = U.shape[1]
+        assert kk > 0
+        assert np.abs(Cm.T @ Cm - np.eye(kk)).max() <= 1e-12
+        AU = np.stack([op(U[:, i]) for i in range(kk)], axis=1)
+        assert np.linalg.norm(AU - Cm) <= 1e-10 * np.linalg.norm(U) * max(1.0, np.linalg.norm(AU))
+        # oracle GCRO-DR on the same operator and the same previous recycle space
+        _, Uo, _, io = ogc.gcrodr(op, c, 30, 8, 1e-10, Ytil=None if Y is None else Y[0], carry=Y)
+        assert abs(its - io.its) <= 0.1 * io.its + 1
+        Y = (U, Cm)
+    F.close()
+
+
+def test_adjoint_and_gradients(pkg):
+    n = 256
+    A = randsvd(n, 1e3, seed=11)
+    b = rhs_uniform(n, 4)
+    xt = normal_vector(n, 5)
+    Ad = cuda(A).requires_grad_(True)
+    bd = cuda(b).requires_grad_(True)
+    prm = pkg.Params(uf="bf16", m=30, k=8, tau=1e-10, target_berr=1e-15)
+    x = pkg.GirSolve.apply(Ad, bd, prm)
+    loss = ((x - cuda(xt)) ** 2).sum()
+    loss.backward()
+    xs = np.linalg.solve(A, b)
+    g = 2 * (xs - xt)
+    lam = np.linalg.solve(A.T, g)
+    db = bd.grad.cpu().numpy()
+    dA = Ad.grad.cpu().numpy()
+    assert np.abs(db - lam).max() <= 1e-8 * np.abs(lam).max()
+    assert np.abs(dA + np.outer(lam, xs)).max() <= 1e-8 * np.abs(np.outer(lam, xs)).max()
+    # central finite differences (h = 1e-6) on sampled entries, through the GPU solve
+    h = 1e-6
+
+    def L(Am, bm):
+        F = pkg.Factorization(cuda(Am), prm)
+        xx, _ = F.solve(cuda(Am), cuda(bm))
+        F.close()
+        return float(((xx.cpu().numpy() - xt) ** 2).sum())
+
+    for (i, j) in [(0, 0), (17, 200), (255, 3)]:
+        Ap, Am = A.copy(), A.copy()
+        Ap[i, j] += h
+        Am[i, j] -= h
+        fd = (L(Ap, b) - L(Am, b)) / (2 * h)
+        assert abs(fd - dA[i, j]) <= 1e-5 * max(1.0, abs(fd))
+    bp, bm = b.copy(), b.copy()
+    bp[9] += h
+    bm[9] -= h
+    fd = (L(A, bp) - L(A, bm)) / (2 * h)
+    assert abs(fd - db[9]) <= 1e-5 * max(1.0, abs(fd))
+
+
+def test_adjoint_matches_oracle(pkg):
+    n = 400
+    A = randsvd(n, 1e3, seed=12)
+    g = rhs_uniform(n, 6)
+    prm = pkg.Params(uf="fp16", m=30, k=8, tau=1e-8, target_berr=1e-15)
+    F = pkg.Factorization(cuda(A), prm)
+    lam, info = F.solve_adjoint(cuda(A), cuda(g))
+    F.close()
+    lam = lam.cpu().numpy()
+    lo, io, _, _ = osolve(A, g, OP(uf="fp16", u="fp64", ur="fp64", ua="u", m=30, k=8, tau=1e-8, target=1e-15,
+                                   lu_w=32), transpose=True)
+    assert info.status == 0 and io.converged
+    assert normwise_berr(A.T, lam, g) <= 4 * max(normwise_berr(A.T, lo, g), UNIT_ROUNDOFF["fp64"])
+    assert abs(info.total_its - io.total) <= 0.1 * io.total + 1
+
+
+def test_batch_uneven(pkg):
+    sizes = [96, 257, 500, 130]
+    As = [randsvd(n, 10 ** (2 + i), seed=n) for i, n in enumerate(sizes)]
+    bs = [rhs_uniform(n, n) for n in sizes]
+    prm = pkg.Params(uf="bf16", m=30, k=8, tau=1e-8, target_berr=1e-15)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    assert st == 0
+    for A, b, x, info in zip(As, bs, xs, infos):
+        assert info.status == 0
+        assert normwise_berr(A, x.cpu().numpy(), b) <= 1e-15
+
+
+def test_status_paths(pkg):
+    from paper_2201_09827_gb300 import gir
+    n = 100
+    A = randsvd(n, 1e3, seed=2)
+    As = A.copy()
+    As[:, 7] = 0.0
+    with pytest.raises(gir.GirError) as e:
+        pkg.Factorization(cuda(As), pkg.Params())
+    assert e.value.status == gir.GIR_SINGULAR
+    An = A.copy()
+    An[3, 3] = np.nan
+    with pytest.raises(gir.GirError) as e:
+        pkg.Factorization(cuda(An), pkg.Params())
+    assert e.value.status == gir.GIR_NONFINITE
+    with pytest.raises(gir.GirError) as e:
+        pkg.Factorization(cuda(A), pkg.Params(m=10, k=10))
+    assert e.value.status == gir.GIR_INVALID_ARG
+    with pytest.raises(gir.GirError) as e:
+        pkg.Factorization(cuda(A), pkg.Params(uf="fp32"))
+    assert e.value.status == gir.GIR_UNSUPPORTED
+    F = pkg.Factorization(cuda(A), pkg.Params(imax=1, target_berr=0.0))
+    x, info = F.solve(cuda(A), cuda(rhs_uniform(n, 0)))
+    assert info.status == gir.GIR_NOT_CONVERGED and info.ir_steps == 1
+    bn = rhs_uniform(n, 0)
+    bn[5] = np.inf
+    x, info = F.solve(cuda(A), cuda(bn))
+    assert info.status == gir.GIR_NONFINITE
+    F.close()
