@@ -191,7 +191,8 @@ gir_status gir_lu_update(float* C, int64_t ldc, const uint16_t* A, int64_t lda, 
 /* Instrumentation (not in the paper). gir_trace_enable(1) records CUDA events on the
  * launching stream around each phase of the factorization and of the solve (no added
  * synchronisation); gir_trace_report writes "phase\tms\tcalls" lines into buf (host,
- * buflen bytes, NUL-terminated), clears the totals and returns the full length needed.
+ * buflen bytes, NUL-terminated), clears the totals and returns the full length needed;
+ * with buf == NULL it only returns the length and keeps the totals.
  * gir_launch_count returns the number of kernels this library has launched so far. */
 void gir_trace_enable(int on);
 int gir_trace_report(char* buf, int buflen);

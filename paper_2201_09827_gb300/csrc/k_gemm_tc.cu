@@ -3,9 +3,10 @@
 //
 // Operands are K-major in global memory: A = L21 rows of the stored factor (row-major, K
 // contiguous) and Bt = U12^T (N x K, K contiguous, written by the TRSM). TMA copies 128-byte
-// swizzled tiles (64 elements of K) into a 4-stage shared-memory ring; one thread issues
+// swizzled tiles (64 elements of K) into a 2-stage shared-memory ring; one thread issues
 // tcgen05.mma (M = 128, N = 256, K = 16 per instruction) into a 128 x 256 FP32 accumulator in
 // tensor memory; tcgen05.commit arrives on the stage's "empty" barrier so TMA can refill it.
+// Two CTAs share an SM (2 x 256 of the 512 TMEM columns).
 // The epilogue (4 warps, one TMEM lane quarter each) reads the accumulator with tcgen05.ld
 // and subtracts it from C. Every mbarrier wait is bounded; a timeout raises a device flag.
 #include <cuda.h>
@@ -20,7 +21,8 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;                   // one 128-byte swizzle atom of 16-bit elements
-constexpr int STAGES = 4;
+constexpr int STAGES = 2;                // ~100 KB shared memory: two CTAs per SM, so one
+                                         // CTA's epilogue overlaps the other's main loop
 constexpr int A_BYTES = BM * BK * 2;     // 16 KB
 constexpr int B_BYTES = BN * BK * 2;     // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -91,7 +93,7 @@ __host__ __device__ constexpr uint32_t make_idesc(int bf16) {
            ((uint32_t)(BM >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
 k_tc_gemm_sub(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* __restrict__ Cm,
               int64_t ldc, int M, int N, int K, uint32_t idesc, int* __restrict__ flags) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];

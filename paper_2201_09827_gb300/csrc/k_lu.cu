@@ -131,7 +131,9 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
         int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelShared<WC>& sh = *reinterpret_cast<PanelShared<WC>*>(smem_raw);
-    float* tile = reinterpret_cast<float*>(smem_raw + sizeof(PanelShared<WC>));  // [rpc][WC]
+    // rows padded to WC + 1 floats so that a warp reading one column of 32 rows hits 32 banks
+    constexpr int TS = WC + 1;
+    float* tile = reinterpret_cast<float*>(smem_raw + sizeof(PanelShared<WC>));  // [rpc][TS]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rank = (int)cluster_nctarank() > 1 ? (int)cluster_ctarank() : 0;
@@ -143,7 +145,7 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     // load own rows (zero-fill columns beyond wcols)
     for (int e = tid; e < myrows * WC; e += PANEL_THREADS) {
         int lr = e / WC, c = e - lr * WC;
-        tile[e] = (c < wcols) ? W[(r0 + g0 + lr) * ldw + r0 + c] : 0.0f;
+        tile[lr * TS + c] = (c < wcols) ? W[(r0 + g0 + lr) * ldw + r0 + c] : 0.0f;
     }
     __syncthreads();
     cluster_barrier();
@@ -157,7 +159,7 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
         for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
             int g = g0 + lr;
             if (g >= j) {
-                float v = fabsf(tile[lr * WC + j]);
+                float v = fabsf(tile[lr * TS + j]);
                 if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
                 if (v > bv || (v == bv && g < bi)) { bv = v; bi = g; }
             }
@@ -188,9 +190,9 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
             const bool own_j = (j >= g0 && j < g0 + myrows);
             for (int e = lane; e < C * WC; e += 32) {
                 int q = e / WC, c = e - q * WC;
-                float val = (clr >= 0) ? tile[clr * WC + c] : 0.0f;
+                float val = (clr >= 0) ? tile[clr * TS + c] : 0.0f;
                 st_cluster_f32(map_shared(&sh.cand_rowv[buf][rank][c], q), val);
-                if (own_j) st_cluster_f32(map_shared(&sh.rowj[buf][c], q), tile[(j - g0) * WC + c]);
+                if (own_j) st_cluster_f32(map_shared(&sh.rowj[buf][c], q), tile[(j - g0) * TS + c]);
             }
         }
         cluster_barrier();
@@ -217,7 +219,7 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
         }
         for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
             int g = g0 + lr;
-            float* row = tile + lr * WC;
+            float* row = tile + lr * TS;
             if (g == j) {
 #pragma unroll
                 for (int c = 0; c < WC; ++c) row[c] = prow[c];
@@ -238,7 +240,7 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     cluster_barrier();
     for (int e = tid; e < myrows * WC; e += PANEL_THREADS) {
         int lr = e / WC, c = e - lr * WC;
-        if (c < wcols) W[(r0 + g0 + lr) * ldw + r0 + c] = tile[e];
+        if (c < wcols) W[(r0 + g0 + lr) * ldw + r0 + c] = tile[lr * TS + c];
     }
     if (local_flag) atomicOr(flags, local_flag);
 }
@@ -287,6 +289,78 @@ __global__ void k_laswp_lower(uint16_t* __restrict__ LU, int64_t ldl, const int*
             LU[k * ldl + j] = b;
             LU[p * ldl + j] = a;
         }
+    }
+}
+
+// ------------------------------------------------------------------ row permutations
+// The interchanges k in [k0, k1) (rows k <-> ipiv[k], applied in order) form one permutation
+// of at most 2 (k1 - k0) rows. k_swap_plan simulates them on row labels (slot table in shared
+// memory, O(1) per interchange) and emits (dst, src) row pairs; k_permute_rows then moves the
+// rows of a column range with coalesced loads and stores (all sources read before any write).
+constexpr int PERM_MAXN = 50000;        // rows addressable by the shared slot table
+constexpr int PERM_MAXK = 512;          // interchanges per plan
+
+__global__ void __launch_bounds__(256) k_swap_plan(const int* __restrict__ ipiv, int64_t k0, int64_t k1,
+                                                   int* __restrict__ plan, int* __restrict__ count) {
+    extern __shared__ int slot_of[];            // indexed by row - k1 for rows >= k1
+    __shared__ int content[2 * PERM_MAXK];
+    __shared__ int rowof[2 * PERM_MAXK];
+    __shared__ int piv_s[PERM_MAXK];
+    const int nk = (int)(k1 - k0);
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        int p = ipiv[k0 + k];
+        piv_s[k] = p;
+        if (p >= k1) slot_of[p - k1] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ns = nk;
+        for (int s = 0; s < nk; ++s) { content[s] = (int)(k0 + s); rowof[s] = (int)(k0 + s); }
+        for (int k = 0; k < nk; ++k) {
+            int p = piv_s[k];
+            if (p >= k1 && slot_of[p - k1] < 0) {
+                slot_of[p - k1] = ns;
+                content[ns] = p;
+                rowof[ns] = p;
+                ++ns;
+            }
+        }
+        for (int k = 0; k < nk; ++k) {
+            int p = piv_s[k];
+            int sa = k, sb = (p < k1) ? (int)(p - k0) : slot_of[p - k1];
+            int t = content[sa];
+            content[sa] = content[sb];
+            content[sb] = t;
+        }
+        int c = 0;
+        for (int s = 0; s < ns; ++s) {
+            if (content[s] != rowof[s]) {
+                plan[2 * c] = rowof[s];
+                plan[2 * c + 1] = content[s];
+                ++c;
+            }
+        }
+        *count = c;
+    }
+}
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(256) k_permute_rows(T* __restrict__ M, int64_t ld, const int* __restrict__ plan,
+                                                      const int* __restrict__ count, int64_t col0, int64_t col1) {
+    extern __shared__ __align__(16) unsigned char prow_raw[];
+    T* buf = reinterpret_cast<T*>(prow_raw);   // [count][CW]
+    const int cnt = *count;
+    const int64_t c0 = col0 + (int64_t)blockIdx.x * CW;
+    if (c0 >= col1) return;
+    const int width = (int)gmin<int64_t>(CW, col1 - c0);
+    for (int e = threadIdx.x; e < cnt * CW; e += blockDim.x) {
+        int r = e / CW, c = e - r * CW;
+        if (c < width) buf[e] = M[(int64_t)plan[2 * r + 1] * ld + c0 + c];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * CW; e += blockDim.x) {
+        int r = e / CW, c = e - r * CW;
+        if (c < width) M[(int64_t)plan[2 * r] * ld + c0 + c] = buf[e];
     }
 }
 
@@ -419,13 +493,48 @@ static gir_status gemm_sub(float* C, int64_t ldc, const uint16_t* A, int64_t lda
     return GIR_OK;
 }
 
+struct SwapScratch {
+    int* plan = nullptr;   // 2 * 2 * PERM_MAXK ints
+    int* count = nullptr;
+};
+
+static gir_status make_plan(const int* ipiv, int64_t k0, int64_t k1, int64_t n, const SwapScratch& sw, cudaStream_t s) {
+    if (k1 - k0 > PERM_MAXK || n - k1 > PERM_MAXN) return GIR_UNSUPPORTED;
+    size_t smem = (size_t)gmax<int64_t>(1, n - k1) * sizeof(int);
+    count_launch(), k_swap_plan<<<1, 256, smem, s>>>(ipiv, k0, k1, sw.plan, sw.count);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+static gir_status permute_f32(float* W, int64_t ldw, int64_t col0, int64_t col1, int64_t maxrows, const SwapScratch& sw,
+                              cudaStream_t s) {
+    if (col1 <= col0) return GIR_OK;
+    constexpr int CW = 32;
+    size_t smem = (size_t)maxrows * CW * sizeof(float);
+    count_launch(), k_permute_rows<float, CW><<<(unsigned)((col1 - col0 + CW - 1) / CW), 256, smem, s>>>(
+        W, ldw, sw.plan, sw.count, col0, col1);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+static gir_status permute_u16(uint16_t* LU, int64_t ldl, int64_t col0, int64_t col1, int64_t maxrows,
+                              const SwapScratch& sw, cudaStream_t s) {
+    if (col1 <= col0) return GIR_OK;
+    constexpr int CW = 64;
+    size_t smem = (size_t)maxrows * CW * sizeof(uint16_t);
+    count_launch(), k_permute_rows<uint16_t, CW><<<(unsigned)((col1 - col0 + CW - 1) / CW), 256, smem, s>>>(
+        LU, ldl, sw.plan, sw.count, col0, col1);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
 static gir_status launch_panel(float* W, int64_t ldw, int64_t c0, int64_t n, int wc, int* ipiv, int* flags,
                                const LUPlan& plan, cudaStream_t s) {
     const int64_t h = n - c0;
     // cluster size: smallest C such that the panel fits the shared-memory budget per CTA
     const int64_t budget = plan.panel_smem_budget;
     const int WC = plan.w;
-    int64_t bytes_per_row = (int64_t)WC * 4;
+    int64_t bytes_per_row = (int64_t)(WC + 1) * 4;  // padded rows (see k_panel)
     int C = (int)((h * bytes_per_row + budget - 1) / budget);
     if (C < 1) C = 1;
     if (C > plan.max_cluster) return GIR_UNSUPPORTED;
@@ -460,7 +569,7 @@ gir_status lu_panel_only(float* W, int64_t ldw, int64_t m, int w, int* ipiv, int
     plan.w = (w <= 16) ? 16 : 32;
     if (cluster > 0) {
         // force the given cluster size through the shared-memory budget
-        int64_t bytes = m * (int64_t)plan.w * 4;
+        int64_t bytes = m * (int64_t)(plan.w + 1) * 4;
         plan.panel_smem_budget = (bytes + cluster - 1) / cluster;
         if (plan.panel_smem_budget < 4) plan.panel_smem_budget = 4;
     }
@@ -485,6 +594,12 @@ gir_status lu_prepare(LUPlan& plan) {
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     plan.panel_smem_budget = 160 * 1024;
     plan.max_cluster = 16;
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_swap_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(PERM_MAXN * sizeof(int))));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_permute_rows<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * PERM_MAXK * 32 * (int)sizeof(float)));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_permute_rows<uint16_t, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * PERM_MAXK * 64 * (int)sizeof(uint16_t)));
     const char* e = getenv("GIR_NO_TC");
     if (e && e[0] == '1') plan.use_tc = 0;  // CUDA-core trailing update (for A/B comparisons)
     return GIR_OK;
@@ -518,7 +633,12 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
     const int w = plan.w;
     const int NB = plan.nb;
     const int64_t ldut = NB;
-    for (int64_t C0 = 0; C0 < n; C0 += NB) {
+    if (NB > PERM_MAXK) return GIR_UNSUPPORTED;
+    SwapScratch sw;
+    GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.plan), 4 * PERM_MAXK * sizeof(int), s));
+    GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.count), sizeof(int), s));
+    gir_status st = GIR_OK;
+    for (int64_t C0 = 0; C0 < n && st == GIR_OK; C0 += NB) {
         const int64_t NBc = gmin<int64_t>(NB, n - C0);
         const int64_t Cend = C0 + NBc;
         for (int64_t c0 = C0; c0 < Cend; c0 += w) {
@@ -529,20 +649,25 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 trace_end(t_, "lu panel", s);
             }
             GIR_TRY(debug_check("panel", C0, c0, flags, s));
+            int t_ = trace_begin(s);
             {
-                int t_ = trace_begin(s);
                 int64_t tot = (n - c0) * wc;
                 int g = (int)gmin<int64_t>((tot + 255) / 256, 152 * 8);
                 count_launch(), k_store_panel<<<g, 256, 0, s>>>(W, ldw, LU, ldl, c0, wc, n, fmt);
-                trace_end(t_, "lu store", s);
             }
+            // this panel's interchanges: on the rest of the outer block (W) and on the L columns
+            // of the earlier panels of the block (stored factor)
+            GIR_TRY(make_plan(ipiv, c0, c0 + wc, n, sw, s));
+            GIR_TRY(permute_f32(W, ldw, c0 + wc, Cend, 2 * wc, sw, s));
+            GIR_TRY(permute_u16(LU, ldl, C0, c0, 2 * wc, sw, s));
+            trace_end(t_, "lu store+swaps", s);
             if (c0 + wc < Cend) {
                 int64_t ncols = Cend - (c0 + wc);
-                int t_ = trace_begin(s);
-                count_launch(), k_laswp_f32<<<(unsigned)((ncols + 127) / 128), 128, 0, s>>>(W, ldw, ipiv, c0, c0 + wc, c0 + wc, Cend);
-                count_launch(), k_trsm_rows<32><<<(unsigned)((ncols + 255) / 256), 256, 0, s>>>(LU, ldl, W, ldw, c0, wc, c0 + wc,
-                                                                                 Cend, fmt, LU, UT + (c0 - C0), ldut);
-                trace_end(t_, "lu inner swap+trsm", s);
+                t_ = trace_begin(s);
+                count_launch(), k_trsm_rows<32><<<(unsigned)((ncols + 255) / 256), 256, 0, s>>>(LU, ldl, W, ldw, c0, wc,
+                                                                                                 c0 + wc, Cend, fmt, LU,
+                                                                                                 UT + (c0 - C0), ldut);
+                trace_end(t_, "lu inner trsm", s);
                 GIR_TRY(debug_check("inner trsm", C0, c0, flags, s));
                 t_ = trace_begin(s);
                 GIR_TRY(gemm_sub(W + (c0 + wc) * ldw + (c0 + wc), ldw, LU + (c0 + wc) * ldl + c0, ldl,
@@ -552,18 +677,20 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 GIR_TRY(debug_check("inner gemm", C0, c0, flags, s));
             }
         }
-        // interchanges of later panels of this outer block on the L columns of earlier ones
+        // the block's interchanges on the trailing columns (W) and on all earlier L columns
         int t_ = trace_begin(s);
-        count_launch(), k_laswp_lower<<<(unsigned)((NBc + 127) / 128), 128, 0, s>>>(LU, ldl, ipiv, C0, Cend, w, C0, Cend, 0, NB);
+        GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, s));
+        GIR_TRY(permute_f32(W, ldw, Cend, n, 2 * NBc, sw, s));
+        GIR_TRY(permute_u16(LU, ldl, 0, C0, 2 * NBc, sw, s));
+        trace_end(t_, "lu outer swaps", s);
         if (Cend < n) {
             const int64_t ntr = n - Cend;
-            count_launch(), k_laswp_f32<<<(unsigned)((ntr + 127) / 128), 128, 0, s>>>(W, ldw, ipiv, C0, Cend, Cend, n);
-            trace_end(t_, "lu outer swaps", s);
             t_ = trace_begin(s);
             for (int64_t b0 = C0; b0 < Cend; b0 += w) {
                 const int wb = (int)gmin<int64_t>(w, Cend - b0);
-                count_launch(), k_trsm_rows<32><<<(unsigned)((ntr + 255) / 256), 256, 0, s>>>(LU, ldl, W, ldw, b0, wb, Cend, n, fmt,
-                                                                               LU, UT + (b0 - C0), ldut);
+                count_launch(), k_trsm_rows<32><<<(unsigned)((ntr + 255) / 256), 256, 0, s>>>(LU, ldl, W, ldw, b0, wb, Cend,
+                                                                                               n, fmt, LU, UT + (b0 - C0),
+                                                                                               ldut);
                 if (b0 + wb < Cend) {
                     GIR_TRY(gemm_sub(W + (b0 + wb) * ldw + Cend, ldw, LU + (b0 + wb) * ldl + b0, ldl,
                                      LU + b0 * ldl + Cend, ldl, UT + Cend * ldut + (b0 - C0), ldut, Cend - (b0 + wb),
@@ -579,12 +706,10 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             GIR_TRY(debug_check("outer gemm", C0, Cend, flags, s));
         }
     }
-    // interchanges of later outer blocks on every L column
-    int t_ = trace_begin(s);
-    count_launch(), k_laswp_lower<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(LU, ldl, ipiv, 0, n, w, 0, n, 1, NB);
-    trace_end(t_, "lu final swaps", s);
+    cudaFreeAsync(sw.plan, s);
+    cudaFreeAsync(sw.count, s);
     GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
+    return st;
 }
 
 }  // namespace gir

@@ -3,11 +3,10 @@
 //
 // Triangular solves are blocked by b = 64 rows. One persistent CTA per block row takes a
 // ticket (atomic counter) in solve order; it streams the off-diagonal tiles of its block row
-// as the solution blocks it depends on are published (per-block ready flags carrying an
-// epoch number), then multiplies by the precomputed inverse of its diagonal block and
-// publishes its own block. A CTA only waits for tickets smaller than its own, which belong to
-// CTAs that are already running, so the scheme cannot deadlock; every wait is bounded and a
-// timeout sets an abort flag that releases all waiters.
+// as the solution elements it depends on are published, then multiplies by the precomputed
+// inverse of its diagonal block and publishes its own block. A CTA only waits for tickets
+// smaller than its own, which belong to CTAs that are already running, so the scheme cannot
+// deadlock; every wait is bounded and a timeout sets an abort flag that releases all waiters.
 #include "gir_internal.cuh"
 #include "k_trsv.cuh"
 
@@ -75,8 +74,27 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 // LOWER: forward order (block I depends on J < I); otherwise backward (J > I).
 // TRANS: the tile of block (I, J) is the transpose of stored tile (J, I).
-// UNIT: diagonal of T is one (only affects the diagonal inverse, precomputed).
-// Input zin: FP64 (zin64) or float-float (zin_ff); output: float-float yout.
+// Input zin: FP64 (zin64) or float-float (zin_ff); output: float-float yout, published
+// element by element: yout starts as the all-ones pattern (an FP32 NaN no computation
+// writes) and each element is written with one 64-bit store, so a consumer polls the data
+// itself instead of a separate flag. The tile of the next dependency is loaded into
+// registers before waiting, and the diagonal-block inverse is staged in shared memory.
+constexpr unsigned long long Y_EMPTY = 0xFFFFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long pack_ff(float h, float l) {
+    if (h != h) h = __int_as_float(0x7fc00000);  // canonical NaN, never the empty pattern
+    if (l != l) l = 0.0f;
+    return ((unsigned long long)__float_as_uint(l) << 32) | (unsigned long long)__float_as_uint(h);
+}
+
 template <bool LOWER, bool TRANS>
 __global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, int64_t ldl, int fmt,
                                               const float2* __restrict__ D, int64_t n, int nblk,
@@ -87,20 +105,26 @@ __global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, i
     __shared__ float acc_h[TB], acc_l[TB];
     __shared__ float yj_h[TB], yj_l[TB];
     __shared__ float red_h[4][TB], red_l[4][TB];
+    __shared__ float2 Ds[TB][TB + 1];
     __shared__ int s_ticket, s_abort;
+    (void)ready;
+    (void)epoch;
+    unsigned long long* ybits = reinterpret_cast<unsigned long long*>(yout);
 
     const int tid = threadIdx.x;
     if (tid == 0) s_ticket = (int)(atomicAdd(ticket_ctr, 1ULL) - base);
     __syncthreads();
     const int t = s_ticket;
     if (t < 0 || t >= nblk) {
-        // ticket counter out of step with the host (a failed earlier launch): give up loudly
         if (tid == 0) { atomicOr(flags, DEV_TIMEOUT); atomicExch(abort_flag, 1); }
         return;
     }
     const int I = LOWER ? t : (nblk - 1 - t);
     const int64_t r0 = (int64_t)I * TB;
-
+    {
+        const float2* Dblk = D + (int64_t)I * TB * TB;
+        for (int e = tid; e < TB * TB; e += 256) Ds[e / TB][e % TB] = Dblk[e];
+    }
     if (tid < TB) {
         int64_t gi = r0 + tid;
         float h = 0.0f, l = 0.0f;
@@ -121,59 +145,57 @@ __global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, i
     if (tid == 0) s_abort = 0;
     __syncthreads();
 
-    // thread mapping for a tile: !TRANS -> row r = tid / 4, column quarter q = tid % 4
-    //                            TRANS  -> row r = tid % 64, stored-row quarter q = tid / 64
     const int r = TRANS ? (tid & 63) : (tid >> 2);
     const int q = TRANS ? (tid >> 6) : (tid & 3);
-
-    for (int step = 0; step < nblk - 1; ++step) {
-        int J;
-        if (LOWER) { J = step; if (J >= I) break; }
-        else { J = nblk - 1 - step; if (J <= I) break; }
-        if (tid == 0) {
-            long long spins = 0;
-            while (ld_acquire(ready + J) != epoch) {
-                if (ld_acquire(abort_flag)) { s_abort = 1; break; }
-                if (++spins > SPIN_LIMIT) {
-                    atomicOr(flags, DEV_TIMEOUT);
-                    atomicExch(abort_flag, 1);
-                    s_abort = 1;
-                    break;
+    float tv[16];
+    auto load_tile = [&](int J) {
+        const int64_t c0 = (int64_t)J * TB;
+        if (!TRANS) {
+            const int64_t gi = r0 + r;
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+                int64_t gc = c0 + q * 16 + cc;
+                tv[cc] = (gi < n && gc < n) ? uf_to_float(LU[gi * ldl + gc], fmt) : 0.0f;
+            }
+        } else {
+            const int64_t gcol = r0 + r;
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+                int64_t grow = c0 + q * 16 + cc;
+                tv[cc] = (gcol < n && grow < n) ? uf_to_float(LU[grow * ldl + gcol], fmt) : 0.0f;
+            }
+        }
+    };
+    const int ndep = LOWER ? I : (nblk - 1 - I);
+    for (int step = 0; step < ndep; ++step) {
+        const int J = LOWER ? step : (nblk - 1 - step);
+        const int64_t c0 = (int64_t)J * TB;
+        load_tile(J);  // independent of y: issued before waiting
+        if (tid < TB) {
+            const int64_t gc = c0 + tid;
+            unsigned long long v = 0ull;
+            if (gc < n) {
+                long long spins = 0;
+                while ((v = ld_relaxed_u64(ybits + gc)) == Y_EMPTY) {
+                    if (((spins & 1023) == 0) && ld_acquire(abort_flag)) { s_abort = 1; break; }
+                    if (++spins > SPIN_LIMIT) {
+                        atomicOr(flags, DEV_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        s_abort = 1;
+                        break;
+                    }
                 }
             }
+            yj_h[tid] = __uint_as_float((unsigned)(v & 0xffffffffull));
+            yj_l[tid] = __uint_as_float((unsigned)(v >> 32));
         }
         __syncthreads();
         if (s_abort) break;
-        const int64_t c0 = (int64_t)J * TB;
-        if (tid < TB) {
-            int64_t gc = c0 + tid;
-            float2 v = (gc < n) ? __ldcg(yout + gc) : make_float2(0.0f, 0.0f);
-            yj_h[tid] = v.x;
-            yj_l[tid] = v.y;
-        }
-        __syncthreads();
         float sh = 0.0f, sl = 0.0f;
-        if (!TRANS) {
-            const int64_t gi = r0 + r;
-            if (gi < n) {
-                const uint16_t* row = LU + gi * ldl + c0 + q * 16;
 #pragma unroll
-                for (int cc = 0; cc < 16; ++cc) {
-                    int c = q * 16 + cc;
-                    if (c0 + c < n) ff_acc_prod1(sh, sl, uf_to_float(row[cc], fmt), yj_h[c], yj_l[c]);
-                }
-            }
-        } else {
-            // element (r, c) of the block-(I,J) tile is stored at LU[(c0 + c), (r0 + r)]
-            const int64_t gcol = r0 + r;
-            if (gcol < n) {
-#pragma unroll 4
-                for (int cc = 0; cc < 16; ++cc) {
-                    int c = q * 16 + cc;
-                    int64_t grow = c0 + c;
-                    if (grow < n) ff_acc_prod1(sh, sl, uf_to_float(LU[grow * ldl + gcol], fmt), yj_h[c], yj_l[c]);
-                }
-            }
+        for (int cc = 0; cc < 16; ++cc) {
+            int c = q * 16 + cc;
+            ff_acc_prod1(sh, sl, tv[cc], yj_h[c], yj_l[c]);
         }
         red_h[q][r] = sh;
         red_l[q][r] = sl;
@@ -192,24 +214,14 @@ __global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, i
         __syncthreads();
     }
 
-    // y_I = D_I acc (TRANS: D_I^T acc); D is the inverse of the stored diagonal block.
+    // y_I = D_I acc (TRANS: D_I^T acc), D staged in shared memory
     {
         float sh = 0.0f, sl = 0.0f;
-        const float2* Dblk = D + (int64_t)I * TB * TB;
-        if (!TRANS) {
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc) {
-                int c = q * 16 + cc;
-                float2 d = Dblk[r * TB + c];
-                ff_acc_prod2(sh, sl, d.x, d.y, acc_h[c], acc_l[c]);
-            }
-        } else {
-#pragma unroll
-            for (int cc = 0; cc < 16; ++cc) {
-                int c = q * 16 + cc;
-                float2 d = Dblk[c * TB + r];
-                ff_acc_prod2(sh, sl, d.x, d.y, acc_h[c], acc_l[c]);
-            }
+        for (int cc = 0; cc < 16; ++cc) {
+            int c = q * 16 + cc;
+            float2 d = TRANS ? Ds[c][r] : Ds[r][c];
+            ff_acc_prod2(sh, sl, d.x, d.y, acc_h[c], acc_l[c]);
         }
         red_h[q][r] = sh;
         red_l[q][r] = sl;
@@ -221,13 +233,8 @@ __global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, i
             ff_acc_add(h, l, red_h[3][tid], red_l[3][tid]);
             ff ns = ff_norm(h, l);
             int64_t gi = r0 + tid;
-            if (gi < n) yout[gi] = make_float2(ns.h, ns.l);
+            if (gi < n) st_relaxed_u64(ybits + gi, s_abort ? pack_ff(0.0f, 0.0f) : pack_ff(ns.h, ns.l));
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        st_release(ready + I, epoch);
     }
 }
 
@@ -306,6 +313,7 @@ static gir_status run_trsv(TrsvState& st, const float2* D, const double* z64, co
     unsigned long long base = st.tickets;
     st.tickets += (unsigned long long)st.nblk;
     int epoch = ++st.epoch;
+    GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
     count_launch(), k_trsv<LOWER, TRANS><<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, st.nblk, z64, zff, y, ready,
                                                  st.ticket_ctr, base, epoch, st.abort_flag, flags);
     st.calls++;

@@ -38,7 +38,11 @@ struct TraceState {
         cudaDeviceSynchronize();
         for (auto& s : slots) {
             float t = 0.0f;
-            if (cudaEventElapsedTime(&t, s.a, s.b) != cudaSuccess) continue;
+            if (!s.name || !s.b) continue;  // a phase that was begun but not ended
+            if (cudaEventElapsedTime(&t, s.a, s.b) != cudaSuccess) {
+                cudaGetLastError();  // do not leave the failure as the runtime's last error
+                continue;
+            }
             bool found = false;
             for (auto& g : agg)
                 if (std::strcmp(g.name, s.name) == 0) {
@@ -103,11 +107,11 @@ int gir_trace_report(char* buf, int buflen) {
         snprintf(line, sizeof(line), "%s\t%.6f\t%lld\n", g.name, g.ms, g.cnt);
         out += line;
     }
-    gir::g_trace.agg.clear();
     if (buf && buflen > 0) {
         int n = (int)out.size() < buflen - 1 ? (int)out.size() : buflen - 1;
         memcpy(buf, out.data(), n);
         buf[n] = 0;
+        gir::g_trace.agg.clear();  // a size query (buf == NULL) keeps the totals
     }
     return (int)out.size();
 }

@@ -163,18 +163,20 @@ def test_factor_properties(G, n, fmt):
 @pytest.mark.parametrize("n,fmt", [(64, "bf16"), (300, "fp16"), (1000, "bf16"), (1031, "fp16")])
 def test_apply_minv_and_atilde(G, n, fmt):
     """With the same (GPU) factors, M^-1 v and M^-1 A v agree with the oracle's FP64 substitution
-    to the float-float accuracy of the triangular solves (about 2^-45 relative)."""
-    A = randsvd(n, 1e4, seed=7)
+    to the float-float accuracy of the triangular solves: about 2^-46 per operation, amplified
+    by the conditioning of the factors (kappa_2(A) = 1e4 here), so 1e-14 * kappa relative."""
+    kappa = 1e4
+    A = randsvd(n, kappa, seed=7)
     F, Fg = _gpu_factors(G, A, fmt)
     rng = np.random.default_rng(8)
     for trans in (False, True):
         v = rng.standard_normal(n)
         w = F.apply_minv(cuda(v), trans=trans).cpu().numpy()
         wo = olu.apply_minv_t(Fg, v) if trans else olu.apply_minv(Fg, v)
-        assert np.abs(w - wo).max() <= 1e-11 * np.abs(wo).max()
+        assert np.abs(w - wo).max() <= 1e-14 * kappa * np.abs(wo).max()
         w = F.apply_atilde(cuda(A), cuda(v), trans=trans).cpu().numpy()
         wo = olu.apply_atilde_t(A, Fg, v) if trans else olu.apply_atilde(A, Fg, v)
-        assert np.abs(w - wo).max() <= 1e-11 * np.abs(wo).max()
+        assert np.abs(w - wo).max() <= 1e-14 * kappa * np.abs(wo).max()
     F.close()
 
 
