@@ -188,6 +188,20 @@ gir_status gir_lu_update(float* C, int64_t ldc, const uint16_t* A, int64_t lda, 
                          const uint16_t* Bt, int64_t ldbt, int64_t M, int64_t N, int64_t K, gir_prec fmt,
                          int use_tc, void* stream);
 
+/* w = A^T v (FP64, device pointers, A row-major with leading dimension lda) for callers that
+ * cannot allocate device memory when they call it (an allocator that forbids cudaMalloc in
+ * a hot loop, a real-time loop, a fixed memory budget). The paper has no counterpart: this is
+ * gir_gemv(trans = 1) with its scratch of partial sums taken from a fixed array in the
+ * library's device image instead of cudaMalloc; the library allocates nothing in this call.
+ * Limit: ceil(n / 256) * n <= 524288 scratch doubles, i.e. n <= 11585; larger n returns
+ * GIR_INVALID_ARG with a message on stderr. The first call on each device looks up the
+ * array's address (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture. All calls share the array: calls whose kernels could overlap on
+ * the GPU (other streams, other host threads) race on it. Enqueued on `stream`; returns
+ * before the kernels finish. Every GPU that loads the library keeps the 4 MiB array until exit. */
+gir_status gir_gemv_t_noalloc(const double* A, int64_t n, int64_t lda, const double* v, double* w,
+                              void* stream);
+
 /* Instrumentation (not in the paper). gir_trace_enable(1) records CUDA events on the
  * launching stream around each phase of the factorization and of the solve (no added
  * synchronisation); gir_trace_report writes "phase\tms\tcalls" lines into buf (host,

@@ -65,6 +65,7 @@ SYMBOLS = {
     "gir_lu_panel": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "gir_lu_update": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                 C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "gir_gemv_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gir_trace_enable": (None, [C.c_int]),
     "gir_trace_report": (C.c_int, [C.c_char_p, C.c_int]),
     "gir_launch_count": (C.c_ulonglong, []),
