@@ -402,6 +402,71 @@ __global__ void __launch_bounds__(256) k_trsm_rows(const uint16_t* __restrict__ 
     }
 }
 
+// Outer TRSM of one block row band: X = L11^-1 W[r0:r0+nb, cols] with L11 the stored unit-lower
+// u_f block (nb <= 256), computed block by block as the per-panel model does: for each 32-row
+// block b, X_b = fl32(L_bb^-1 X_b) by FP32 substitution, U_b = fl_uf(X_b) (stored in LU, UT and
+// used from then on), and the rows below are updated with the u_f operands L[.., b] and U_b
+// (FP32 accumulation). One CTA per 64 columns; L11 and the column slab live in shared memory.
+constexpr int TB_COLS = 64;
+constexpr int TB_MAXNB = 256;
+
+__global__ void __launch_bounds__(256) k_trsm_band(const uint16_t* __restrict__ LU, int64_t ldl, float* __restrict__ W,
+                                                   int64_t ldw, int64_t r0, int nb, int w, int64_t col0, int64_t col1,
+                                                   int fmt, uint16_t* __restrict__ LUout, uint16_t* __restrict__ UT,
+                                                   int64_t ldut) {
+    extern __shared__ __align__(16) unsigned char tb_raw[];
+    uint16_t* Ls = reinterpret_cast<uint16_t*>(tb_raw);                            // [nb][nb]
+    float* X = reinterpret_cast<float*>(tb_raw + (size_t)TB_MAXNB * TB_MAXNB * 2); // [nb][TB_COLS + 1]
+    constexpr int XS = TB_COLS + 1;
+    const int tid = threadIdx.x;
+    const int64_t c0 = col0 + (int64_t)blockIdx.x * TB_COLS;
+    const int width = (int)gmin<int64_t>(TB_COLS, col1 - c0);
+    for (int e = tid; e < nb * nb; e += 256) {
+        int i = e / nb, q = e - i * nb;
+        Ls[e] = (q < i) ? LU[(r0 + i) * ldl + r0 + q] : (uint16_t)0;
+    }
+    for (int e = tid; e < nb * TB_COLS; e += 256) {
+        int i = e / TB_COLS, c = e - i * TB_COLS;
+        X[i * XS + c] = (c < width) ? W[(r0 + i) * ldw + c0 + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += w) {
+        const int wb = min(w, nb - b0);
+        // substitution inside the block: thread per column (FP32 fused updates)
+        if (tid < TB_COLS) {
+            const int c = tid;
+            for (int i = 1; i < wb; ++i) {
+                float acc = X[(b0 + i) * XS + c];
+                for (int q = 0; q < i; ++q) acc = fmaf(-uf_to_float(Ls[(b0 + i) * nb + b0 + q], fmt), X[(b0 + q) * XS + c], acc);
+                X[(b0 + i) * XS + c] = acc;
+            }
+        }
+        __syncthreads();
+        // round the block to u_f: stored factor, transposed operand, and the value used below
+        for (int e = tid; e < wb * TB_COLS; e += 256) {
+            int i = e / TB_COLS, c = e - i * TB_COLS;
+            uint16_t u = float_to_uf(X[(b0 + i) * XS + c], fmt);
+            float uv = uf_to_float(u, fmt);
+            X[(b0 + i) * XS + c] = uv;
+            if (c < width) {
+                LUout[(r0 + b0 + i) * ldl + c0 + c] = u;
+                W[(r0 + b0 + i) * ldw + c0 + c] = uv;
+                UT[(c0 + c) * ldut + b0 + i] = u;
+            }
+        }
+        __syncthreads();
+        // rows below the block: X[i] -= L[i, b0:b0+wb] U_b
+        const int rows_below = nb - (b0 + wb);
+        for (int e = tid; e < rows_below * TB_COLS; e += 256) {
+            int i = b0 + wb + e / TB_COLS, c = e % TB_COLS;
+            float acc = 0.0f;
+            for (int q = 0; q < wb; ++q) acc = fmaf(uf_to_float(Ls[i * nb + b0 + q], fmt), X[(b0 + q) * XS + c], acc);
+            X[i * XS + c] -= acc;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ SIMT trailing update
 // C[M x N] -= A[M x K] * B[K x N] with u_f operands (16-bit, row-major) and FP32 accumulation.
 // 128 x 128 tile, BK = 16, 256 threads, 8 x 8 outputs per thread.
@@ -594,6 +659,8 @@ gir_status lu_prepare(LUPlan& plan) {
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     plan.panel_smem_budget = 160 * 1024;
     plan.max_cluster = 16;
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TB_MAXNB * TB_MAXNB * 2 + TB_MAXNB * (TB_COLS + 1) * 4));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_swap_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(PERM_MAXN * sizeof(int))));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_permute_rows<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -628,16 +695,43 @@ gir_status lu_scale_quantize(const double* A, int64_t n, int64_t lda, int uf, do
     return GIR_OK;
 }
 
+// Look-ahead schedule: block k's trailing update is split into (a) the next block's columns,
+// on the main stream, and (b) all later columns, on a side stream, so (b) runs while the next
+// block's panels (a few SMs) are factored. Events keep every W update, row interchange and
+// UT access ordered: (b)_k finishes before block k+1's end-of-block interchanges and (a)_{k+1}.
 gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv, int64_t n, int fmt,
                      const LUPlan& plan, uint16_t* UT, int* flags, cudaStream_t s) {
     const int w = plan.w;
     const int NB = plan.nb;
     const int64_t ldut = NB;
-    if (NB > PERM_MAXK) return GIR_UNSUPPORTED;
+    if (NB > PERM_MAXK || NB > TB_MAXNB) return GIR_UNSUPPORTED;
     SwapScratch sw;
+    // side stream and events, released on every return path (work still queued completes first)
+    struct Side {
+        cudaStream_t s2 = nullptr;
+        cudaEvent_t ev_swapped = nullptr, ev_b = nullptr;
+        ~Side() {
+            if (ev_swapped) cudaEventDestroy(ev_swapped);
+            if (ev_b) cudaEventDestroy(ev_b);
+            if (s2) cudaStreamDestroy(s2);
+        }
+    } side;
+    cudaStream_t& s2 = side.s2;
+    cudaEvent_t& ev_swapped = side.ev_swapped;
+    cudaEvent_t& ev_b = side.ev_b;
+    GIR_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ev_swapped, cudaEventDisableTiming));
+    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming));
     GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.plan), 4 * PERM_MAXK * sizeof(int), s));
     GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.count), sizeof(int), s));
+    bool b_pending = false;  // a (b) part is running on s2
     gir_status st = GIR_OK;
+    auto trsm_band = [&](int64_t C0, int64_t NBc, int64_t col0, int64_t col1, cudaStream_t ss) {
+        if (col1 <= col0) return;
+        const size_t smem = (size_t)TB_MAXNB * TB_MAXNB * 2 + (size_t)NBc * (TB_COLS + 1) * 4;
+        count_launch(), k_trsm_band<<<(unsigned)((col1 - col0 + TB_COLS - 1) / TB_COLS), 256, smem, ss>>>(
+            LU, ldl, W, ldw, C0, (int)NBc, w, col0, col1, fmt, LU, UT, ldut);
+    };
     for (int64_t C0 = 0; C0 < n && st == GIR_OK; C0 += NB) {
         const int64_t NBc = gmin<int64_t>(NB, n - C0);
         const int64_t Cend = C0 + NBc;
@@ -655,8 +749,6 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 int g = (int)gmin<int64_t>((tot + 255) / 256, 152 * 8);
                 count_launch(), k_store_panel<<<g, 256, 0, s>>>(W, ldw, LU, ldl, c0, wc, n, fmt);
             }
-            // this panel's interchanges: on the rest of the outer block (W) and on the L columns
-            // of the earlier panels of the block (stored factor)
             GIR_TRY(make_plan(ipiv, c0, c0 + wc, n, sw, s));
             GIR_TRY(permute_f32(W, ldw, c0 + wc, Cend, 2 * wc, sw, s));
             GIR_TRY(permute_u16(LU, ldl, C0, c0, 2 * wc, sw, s));
@@ -677,7 +769,12 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 GIR_TRY(debug_check("inner gemm", C0, c0, flags, s));
             }
         }
-        // the block's interchanges on the trailing columns (W) and on all earlier L columns
+        // the previous block's (b) part touches the trailing W columns and reads L rows of that
+        // block: it must finish before this block's interchanges move those rows
+        if (b_pending) {
+            GIR_CUDA_TRY(cudaStreamWaitEvent(s, ev_b, 0));
+            b_pending = false;
+        }
         int t_ = trace_begin(s);
         GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, s));
         GIR_TRY(permute_f32(W, ldw, Cend, n, 2 * NBc, sw, s));
@@ -685,27 +782,34 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
         trace_end(t_, "lu outer swaps", s);
         if (Cend < n) {
             const int64_t ntr = n - Cend;
+            const int64_t Ca = gmin<int64_t>(n, Cend + NB);  // (a): columns [Cend, Ca)
+            // (a) on the main stream: the next block's columns
             t_ = trace_begin(s);
-            for (int64_t b0 = C0; b0 < Cend; b0 += w) {
-                const int wb = (int)gmin<int64_t>(w, Cend - b0);
-                count_launch(), k_trsm_rows<32><<<(unsigned)((ntr + 255) / 256), 256, 0, s>>>(LU, ldl, W, ldw, b0, wb, Cend,
-                                                                                               n, fmt, LU, UT + (b0 - C0),
-                                                                                               ldut);
-                if (b0 + wb < Cend) {
-                    GIR_TRY(gemm_sub(W + (b0 + wb) * ldw + Cend, ldw, LU + (b0 + wb) * ldl + b0, ldl,
-                                     LU + b0 * ldl + Cend, ldl, UT + Cend * ldut + (b0 - C0), ldut, Cend - (b0 + wb),
-                                     ntr, wb, fmt, plan, flags, s));
-                }
-            }
+            trsm_band(C0, NBc, Cend, Ca, s);
             trace_end(t_, "lu outer trsm", s);
-            GIR_TRY(debug_check("outer trsm", C0, Cend, flags, s));
+            GIR_TRY(debug_check("outer trsm a", C0, Cend, flags, s));
             t_ = trace_begin(s);
             GIR_TRY(gemm_sub(W + Cend * ldw + Cend, ldw, LU + Cend * ldl + C0, ldl, LU + C0 * ldl + Cend, ldl,
-                             UT + Cend * ldut, ldut, ntr, ntr, NBc, fmt, plan, flags, s));
+                             UT + Cend * ldut, ldut, ntr, Ca - Cend, NBc, fmt, plan, flags, s));
             trace_end(t_, "lu outer gemm", s);
+            if (Ca < n) {
+                // (b) on the side stream, after this block's interchanges
+                GIR_CUDA_TRY(cudaEventRecord(ev_swapped, s));
+                GIR_CUDA_TRY(cudaStreamWaitEvent(s2, ev_swapped, 0));
+                int tb = trace_begin(s2);
+                trsm_band(C0, NBc, Ca, n, s2);
+                trace_end(tb, "lu outer trsm", s2);
+                tb = trace_begin(s2);
+                GIR_TRY(gemm_sub(W + Cend * ldw + Ca, ldw, LU + Cend * ldl + C0, ldl, LU + C0 * ldl + Ca, ldl,
+                                 UT + Ca * ldut, ldut, ntr, n - Ca, NBc, fmt, plan, flags, s2));
+                trace_end(tb, "lu outer gemm", s2);
+                GIR_CUDA_TRY(cudaEventRecord(ev_b, s2));
+                b_pending = true;
+            }
             GIR_TRY(debug_check("outer gemm", C0, Cend, flags, s));
         }
     }
+    if (b_pending) GIR_CUDA_TRY(cudaStreamWaitEvent(s, ev_b, 0));
     cudaFreeAsync(sw.plan, s);
     cudaFreeAsync(sw.count, s);
     GIR_CUDA_TRY(cudaGetLastError());
