@@ -123,174 +123,293 @@ struct PanelShared {
     float rowj[2][WC];
     float wbest_val[2][PANEL_THREADS / 32];
     int wbest_row[2][PANEL_THREADS / 32];
+    int piv[WC];                      // panel-relative pivot row of each column
+    float top[WC][WC + 1];            // final rows 0..wcols-1 of the panel (L11 below the diagonal)
+    int ext_row[32];                  // distinct pivot rows below the panel's diagonal block
+    int mv_dst[64], mv_src[64];       // net row moves of the panel's interchanges
+    int mv_count;
 };
 
+// Work the panel kernel does once its columns are factored: store the u_f copy of the panel into
+// LU, apply the panel's row interchanges to other columns of W (FP32) and LU (u_f), and solve
+// for the U12 rows of the W columns.
+struct PanelTail {
+    uint16_t* LU;          // null: no u_f store and no LU interchanges
+    int64_t ldl;
+    int fmt;
+    int64_t wcol0, wcol1;  // W columns [wcol0, wcol1) receive the interchanges
+    int64_t lcol0, lcol1;  // LU columns [lcol0, lcol1) receive them
+    uint16_t* UT;          // non-null: also U12 = fl_uf(L11^-1 W[panel rows, wcol0:wcol1]) into
+    int64_t ldut;          //   LU, W and UT[col * ldut + i] (FP32 substitution, then rounded)
+};
+
+__device__ __forceinline__ void argmax_merge(float& v, int& r, float ov, int orow) {
+    if (ov > v || (ov == v && orow < r)) { v = ov; r = orow; }
+}
+
+// GEPP of one FP32 panel (rows r0..n-1, wcols <= WC columns) by a cluster of C CTAs, each holding
+// rpc consecutive rows in shared memory. Per column: thread-owned rows give local candidates
+// (computed while the previous column's update ran), one CTA barrier merges them, every CTA
+// pushes its candidate (value, row, row values) and, if it owns row j, row j into every CTA's
+// slot through DSMEM, and one cluster barrier publishes them. Every warp then picks the global
+// pivot (largest |value|, lowest row on ties) and updates its rows with correctly rounded FP32
+// quotients and fused updates: the FP32 Schur complement of the block-FMA model (Section 3).
 template <int WC>
 __global__ void __launch_bounds__(PANEL_THREADS, 1)
 k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, int rpc, int* __restrict__ ipiv,
-        int* __restrict__ flags) {
+        int* __restrict__ flags, PanelTail tail) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelShared<WC>& sh = *reinterpret_cast<PanelShared<WC>*>(smem_raw);
     // rows padded to WC + 1 floats so that a warp reading one column of 32 rows hits 32 banks
     constexpr int TS = WC + 1;
+    constexpr int NW = PANEL_THREADS / 32;
+    constexpr int NONE = 0x7fffffff;
     float* tile = reinterpret_cast<float*>(smem_raw + sizeof(PanelShared<WC>));  // [rpc][TS]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rank = (int)cluster_nctarank() > 1 ? (int)cluster_ctarank() : 0;
     const int C = (int)cluster_nctarank();
+    const int rank = C > 1 ? (int)cluster_ctarank() : 0;
     const int64_t h = n - r0;
     const int g0 = rank * rpc;                              // first panel row of this CTA
     const int myrows = (int)gmax<int64_t>(0, gmin<int64_t>(rpc, h - g0));
 
-    // load own rows (zero-fill columns beyond wcols)
     for (int e = tid; e < myrows * WC; e += PANEL_THREADS) {
         int lr = e / WC, c = e - lr * WC;
         tile[lr * TS + c] = (c < wcols) ? W[(r0 + g0 + lr) * ldw + r0 + c] : 0.0f;
     }
     __syncthreads();
-    cluster_barrier();
-
     int local_flag = 0;
+    float bv = -1.0f;
+    int bi = NONE;
+    for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
+        float v = fabsf(tile[lr * TS]);
+        if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
+        argmax_merge(bv, bi, v, g0 + lr);
+    }
+    cluster_barrier();   // every CTA of the cluster is running before the first remote store
+
     for (int j = 0; j < wcols; ++j) {
         const int buf = j & 1;
-        // local argmax over own rows with panel row >= j
-        float bv = -1.0f;
-        int bi = 0x7fffffff;
-        for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
-            int g = g0 + lr;
-            if (g >= j) {
-                float v = fabsf(tile[lr * TS + j]);
-                if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
-                if (v > bv || (v == bv && g < bi)) { bv = v; bi = g; }
-            }
-        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             float ov = __shfl_xor_sync(0xffffffffu, bv, o);
             int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            argmax_merge(bv, bi, ov, oi);
         }
         if (lane == 0) { sh.wbest_val[buf][warp] = bv; sh.wbest_row[buf][warp] = bi; }
         __syncthreads();
-        if (warp == 0) {
-            float v = (lane < PANEL_THREADS / 32) ? sh.wbest_val[buf][lane] : -1.0f;
-            int r = (lane < PANEL_THREADS / 32) ? sh.wbest_row[buf][lane] : 0x7fffffff;
+        // this CTA's candidate, merged redundantly by every warp
+        float cv = (lane < NW) ? sh.wbest_val[buf][lane] : -1.0f;
+        int cr = (lane < NW) ? sh.wbest_row[buf][lane] : NONE;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                float ov = __shfl_xor_sync(0xffffffffu, v, o);
-                int oi = __shfl_xor_sync(0xffffffffu, r, o);
-                if (ov > v || (ov == v && oi < r)) { v = ov; r = oi; }
-            }
-            // candidate (value, row) to every CTA's slot [rank]
-            if (lane < C) {
-                st_cluster_f32(map_shared(&sh.cand_val[buf][rank], lane), v);
-                st_cluster_s32(map_shared(&sh.cand_row[buf][rank], lane), r);
-            }
-            const int clr = (r != 0x7fffffff) ? r - g0 : -1;
-            const bool own_j = (j >= g0 && j < g0 + myrows);
-            for (int e = lane; e < C * WC; e += 32) {
-                int q = e / WC, c = e - q * WC;
-                float val = (clr >= 0) ? tile[clr * TS + c] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            float ov = __shfl_xor_sync(0xffffffffu, cv, o);
+            int oi = __shfl_xor_sync(0xffffffffu, cr, o);
+            argmax_merge(cv, cr, ov, oi);
+        }
+        {
+            const int q = tid / WC, c = tid - (tid / WC) * WC;   // destination CTA, column
+            if (q < C) {
+                if (c == 0) {
+                    st_cluster_f32(map_shared(&sh.cand_val[buf][rank], q), cv);
+                    st_cluster_s32(map_shared(&sh.cand_row[buf][rank], q), cr);
+                }
+                const float val = (cr != NONE) ? tile[(cr - g0) * TS + c] : 0.0f;
                 st_cluster_f32(map_shared(&sh.cand_rowv[buf][rank][c], q), val);
-                if (own_j) st_cluster_f32(map_shared(&sh.rowj[buf][c], q), tile[(j - g0) * TS + c]);
+                if (j >= g0 && j < g0 + myrows)
+                    st_cluster_f32(map_shared(&sh.rowj[buf][c], q), tile[(j - g0) * TS + c]);
             }
         }
         cluster_barrier();
-        // global winner
-        float pv = -1.0f;
-        int pr = 0x7fffffff, pq = 0;
-        for (int q = 0; q < C; ++q) {
-            float v = sh.cand_val[buf][q];
-            int r = sh.cand_row[buf][q];
-            if (v > pv || (v == pv && r < pr)) { pv = v; pr = r; pq = q; }
+        // global pivot, merged redundantly by every warp
+        float pv = (lane < C) ? sh.cand_val[buf][lane] : -1.0f;
+        int pr = (lane < C) ? sh.cand_row[buf][lane] : NONE;
+        int pq = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float ov = __shfl_xor_sync(0xffffffffu, pv, o);
+            int oi = __shfl_xor_sync(0xffffffffu, pr, o);
+            int oq = __shfl_xor_sync(0xffffffffu, pq, o);
+            if (ov > pv || (ov == pv && oi < pr)) { pv = ov; pr = oi; pq = oq; }
         }
-        if (pr == 0x7fffffff) {
+        if (pr == NONE) {
             // no finite candidate in the column (all NaN): keep the row order, flag, divide by nothing
             pr = j;
             pv = 0.0f;
+            pq = 0;
             local_flag |= DEV_NONFINITE;
         }
+        if (pq >= C) pq = 0;
         const float* prow = sh.cand_rowv[buf][pq];
         const float* rj = sh.rowj[buf];
         const float piv = prow[j];
-        if (tid == 0 && rank == 0) {
-            ipiv[r0 + j] = (int)(r0 + pr);
+        if (tid < WC) sh.top[j][tid] = prow[tid];   // row j of the panel is final from here on
+        if (tid == 0) {
+            sh.piv[j] = pr;
+            if (rank == 0) ipiv[r0 + j] = (int)(r0 + pr);
             if (pv == 0.0f) local_flag |= DEV_SINGULAR;
         }
+        float pc[WC];
+#pragma unroll
+        for (int c = 0; c < WC; ++c) pc[c] = prow[c];
+        const bool next = j + 1 < wcols;
+        bv = -1.0f;
+        bi = NONE;
         for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
-            int g = g0 + lr;
+            const int g = g0 + lr;
             float* row = tile + lr * TS;
             if (g == j) {
 #pragma unroll
-                for (int c = 0; c < WC; ++c) row[c] = prow[c];
+                for (int c = 0; c < WC; ++c) row[c] = pc[c];
             } else if (g == pr) {
 #pragma unroll
                 for (int c = 0; c < WC; ++c) row[c] = rj[c];
             }
             if (g > j) {
-                float l = (piv != 0.0f) ? __fdiv_rn(row[j], piv) : 0.0f;
+                const float l = (piv != 0.0f) ? __fdiv_rn(row[j], piv) : 0.0f;
                 row[j] = l;
 #pragma unroll
-                for (int c = 0; c < WC; ++c)
-                    if (c > j) row[c] = fmaf(-l, prow[c], row[c]);
+                for (int cb = 0; cb < WC; cb += 8) {
+                    if (cb + 7 > j) {
+#pragma unroll
+                        for (int c = cb; c < cb + 8; ++c)
+                            if (c > j) row[c] = fmaf(-l, pc[c], row[c]);
+                    }
+                }
+                if (next) {
+                    float v = fabsf(row[j + 1]);
+                    if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
+                    argmax_merge(bv, bi, v, g);
+                }
             }
         }
-        __syncthreads();
     }
-    cluster_barrier();
+    // no remote access after the last cluster barrier: every CTA finishes on its own
+    __syncthreads();
     for (int e = tid; e < myrows * WC; e += PANEL_THREADS) {
         int lr = e / WC, c = e - lr * WC;
-        if (c < wcols) W[(r0 + g0 + lr) * ldw + r0 + c] = tile[lr * TS + c];
+        if (c < wcols) {
+            const float v = tile[lr * TS + c];
+            W[(r0 + g0 + lr) * ldw + r0 + c] = v;
+            if (tail.LU) tail.LU[(r0 + g0 + lr) * tail.ldl + r0 + c] = float_to_uf(v, tail.fmt);
+        }
     }
     if (local_flag) atomicOr(flags, local_flag);
-}
 
-// ------------------------------------------------------------------ stores, swaps, TRSM
-// LU16[r][c0 + c] = fl_uf(W[r][c0 + c]) for panel rows r in [c0, n), c < wc.
-__global__ void k_store_panel(const float* __restrict__ W, int64_t ldw, uint16_t* __restrict__ LU, int64_t ldl,
-                              int64_t c0, int wc, int64_t n, int fmt) {
-    const int64_t rows = n - c0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * wc; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = c0 + e / wc;
-        int c = (int)(e % wc);
-        LU[r * ldl + c0 + c] = float_to_uf(W[r * ldw + c0 + c], fmt);
+    const int64_t ncw = tail.wcol1 - tail.wcol0;
+    const int64_t ncl = tail.LU ? tail.lcol1 - tail.lcol0 : 0;
+    if (ncw <= 0 && ncl <= 0) return;
+    // net effect of the interchanges ipiv[r0 .. r0+wcols) as row moves (dst <- src): replay them
+    // on slot contents held in one warp's registers (slots 0..31 panel rows, 32.. the distinct
+    // pivot rows below the diagonal block, numbered by first use)
+    if (warp == 0) {
+        const unsigned FULL = 0xffffffffu;
+        const int p = (lane < wcols) ? sh.piv[lane] : lane;
+        const bool ext = lane < wcols && p >= wcols;
+        const unsigned key = ext ? (unsigned)p : (0x80000000u | (unsigned)lane);
+        const unsigned same = __match_any_sync(FULL, key);
+        const int first = __ffs(same) - 1;
+        const unsigned leaders = __ballot_sync(FULL, ext && first == lane);
+        const int nlead = __popc(leaders);
+        const int slot = ext ? 32 + __popc(leaders & ((1u << first) - 1u)) : p;
+        if (ext && first == lane) sh.ext_row[__popc(leaders & ((1u << lane) - 1u))] = p;
+        __syncwarp();
+        const int rowB = (lane < nlead) ? sh.ext_row[lane] : -1;
+        int cA = lane, cB = rowB;
+        for (int k = 0; k < wcols; ++k) {
+            const int b = __shfl_sync(FULL, slot, k);
+            const int va = __shfl_sync(FULL, cA, k);
+            const int vbA = __shfl_sync(FULL, cA, b & 31);
+            const int vbB = __shfl_sync(FULL, cB, b & 31);
+            const int vb = (b < 32) ? vbA : vbB;
+            if (lane == k) cA = vb;
+            if (b < 32) {
+                if (lane == b) cA = va;
+            } else if (lane == b - 32) {
+                cB = va;
+            }
+        }
+        const bool mA = lane < wcols && cA != lane;
+        const bool mB = lane < nlead && cB != rowB;
+        const unsigned bA = __ballot_sync(FULL, mA), bB = __ballot_sync(FULL, mB);
+        const unsigned lt = (1u << lane) - 1u;
+        if (mA) { int i = __popc(bA & lt); sh.mv_dst[i] = lane; sh.mv_src[i] = cA; }
+        if (mB) { int i = __popc(bA) + __popc(bB & lt); sh.mv_dst[i] = rowB; sh.mv_src[i] = cB; }
+        if (lane == 0) sh.mv_count = __popc(bA) + __popc(bB);
     }
-}
-
-// Apply interchanges k in [k0, k1) (rows k <-> ipiv[k]) to W columns [col0, col1).
-__global__ void k_laswp_f32(float* __restrict__ W, int64_t ldw, const int* __restrict__ ipiv, int64_t k0,
-                            int64_t k1, int64_t col0, int64_t col1) {
-    const int64_t j = col0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= col1) return;
-    for (int64_t k = k0; k < k1; ++k) {
-        int64_t p = ipiv[k];
-        if (p != k) {
-            float a = W[k * ldw + j], b = W[p * ldw + j];
-            W[k * ldw + j] = b;
-            W[p * ldw + j] = a;
+    __syncthreads();
+    const int cnt = sh.mv_count;
+    const bool trsm = tail.UT != nullptr;
+    if (cnt == 0 && !trsm) return;
+    // column chunks (32 FP32 columns of W, 64 u_f columns of LU) spread over the cluster's CTAs;
+    // every source of a chunk is read before any destination is written
+    const int nchw = (int)((gmax<int64_t>(ncw, 0) + 31) / 32);
+    const int nchl = (int)((gmax<int64_t>(ncl, 0) + 63) / 64);
+    for (int ch = rank; ch < nchw + nchl; ch += C) {
+        if (ch < nchw) {
+            const int64_t cbase = tail.wcol0 + (int64_t)ch * 32;
+            if (cnt > 0) {
+                float v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 5;
+                    const int64_t col = cbase + (e & 31);
+                    if (m < cnt && col < tail.wcol1) v[k] = W[(r0 + sh.mv_src[m]) * ldw + col];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 5;
+                    const int64_t col = cbase + (e & 31);
+                    if (m < cnt && col < tail.wcol1) W[(r0 + sh.mv_dst[m]) * ldw + col] = v[k];
+                }
+                __syncthreads();
+            }
+            if (trsm && tid < 32 && cbase + tid < tail.wcol1) {
+                // forward substitution with the u_f multipliers, one thread per column
+                const int64_t col = cbase + tid;
+                float x[WC];
+#pragma unroll
+                for (int i = 0; i < WC; ++i) x[i] = (i < wcols) ? W[(r0 + i) * ldw + col] : 0.0f;
+#pragma unroll
+                for (int i = 1; i < WC; ++i) {
+                    float acc = x[i];
+#pragma unroll
+                    for (int q = 0; q < WC; ++q)
+                        if (q < i) acc = fmaf(-uf_to_float(float_to_uf(sh.top[i][q], tail.fmt), tail.fmt), x[q], acc);
+                    x[i] = acc;
+                }
+#pragma unroll
+                for (int i = 0; i < WC; ++i) {
+                    if (i < wcols) {
+                        const uint16_t u = float_to_uf(x[i], tail.fmt);
+                        tail.LU[(r0 + i) * tail.ldl + col] = u;
+                        W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
+                        tail.UT[col * tail.ldut + i] = u;
+                    }
+                }
+            }
+        } else if (cnt > 0) {
+            const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw) * 64;
+            uint16_t v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = tid + k * PANEL_THREADS, m = e >> 6;
+                const int64_t col = cbase + (e & 63);
+                if (m < cnt && col < tail.lcol1) v[k] = tail.LU[(r0 + sh.mv_src[m]) * tail.ldl + col];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int e = tid + k * PANEL_THREADS, m = e >> 6;
+                const int64_t col = cbase + (e & 63);
+                if (m < cnt && col < tail.lcol1) tail.LU[(r0 + sh.mv_dst[m]) * tail.ldl + col] = v[k];
+            }
         }
     }
 }
 
-// Row interchanges of later panels applied to the stored L columns: column j (panel
-// [j/w*w, j/w*w + w)) sees the interchanges k in [max(kbeg, (j/w + 1) w), kend).
-// Within an outer block this runs before the block's L21 feeds the outer update; the final
-// pass covers the interchanges of later outer blocks.
-__global__ void k_laswp_lower(uint16_t* __restrict__ LU, int64_t ldl, const int* __restrict__ ipiv, int64_t col0,
-                              int64_t col1, int w, int64_t kbeg, int64_t kend, int per_outer, int64_t nb) {
-    const int64_t j = col0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= col1) return;
-    int64_t k0 = per_outer ? (j / nb + 1) * nb : (j / w + 1) * w;
-    if (k0 < kbeg) k0 = kbeg;
-    for (int64_t k = k0; k < kend; ++k) {
-        int64_t p = ipiv[k];
-        if (p != k) {
-            uint16_t a = LU[k * ldl + j], b = LU[p * ldl + j];
-            LU[k * ldl + j] = b;
-            LU[p * ldl + j] = a;
-        }
-    }
-}
+// ------------------------------------------------------------------ swaps, TRSM
 
 // ------------------------------------------------------------------ row permutations
 // The interchanges k in [k0, k1) (rows k <-> ipiv[k], applied in order) form one permutation
@@ -298,7 +417,7 @@ __global__ void k_laswp_lower(uint16_t* __restrict__ LU, int64_t ldl, const int*
 // memory, O(1) per interchange) and emits (dst, src) row pairs; k_permute_rows then moves the
 // rows of a column range with coalesced loads and stores (all sources read before any write).
 constexpr int PERM_MAXN = 50000;        // rows addressable by the shared slot table
-constexpr int PERM_MAXK = 512;          // interchanges per plan
+constexpr int PERM_MAXK = 256;          // interchanges per plan (outer block width)
 
 __global__ void __launch_bounds__(256) k_swap_plan(const int* __restrict__ ipiv, int64_t k0, int64_t k1,
                                                    int* __restrict__ plan, int* __restrict__ count) {
@@ -306,99 +425,120 @@ __global__ void __launch_bounds__(256) k_swap_plan(const int* __restrict__ ipiv,
     __shared__ int content[2 * PERM_MAXK];
     __shared__ int rowof[2 * PERM_MAXK];
     __shared__ int piv_s[PERM_MAXK];
+    __shared__ int slot_s[PERM_MAXK];
+    __shared__ int scan_s[2 * PERM_MAXK];
+    __shared__ int warp_tot[8];
     const int nk = (int)(k1 - k0);
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k < nk; k += 256) {
         int p = ipiv[k0 + k];
         piv_s[k] = p;
-        if (p >= k1) slot_of[p - k1] = -1;
+        if (p >= k1) slot_of[p - k1] = 0x7fffffff;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int ns = nk;
-        for (int s = 0; s < nk; ++s) { content[s] = (int)(k0 + s); rowof[s] = (int)(k0 + s); }
-        for (int k = 0; k < nk; ++k) {
-            int p = piv_s[k];
-            if (p >= k1 && slot_of[p - k1] < 0) {
-                slot_of[p - k1] = ns;
-                content[ns] = p;
-                rowof[ns] = p;
-                ++ns;
-            }
+    // the first interchange that names a row below the block owns that row's slot
+    for (int k = tid; k < nk; k += 256) {
+        int p = piv_s[k];
+        if (p >= k1) atomicMin(&slot_of[p - k1], k);
+    }
+    __syncthreads();
+    // number the distinct rows below the block in order of first use (block scan of leader flags)
+    auto block_scan = [&](int* flag, int len) -> int {   // exclusive scan in place, returns total
+        const int per = (len + 255) / 256;               // contiguous items per thread
+        int local = 0;
+        for (int i = 0; i < per; ++i) { int k = tid * per + i; if (k < len) local += flag[k]; }
+        int incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) { int t = __shfl_up_sync(0xffffffffu, incl, o); if (lane >= o) incl += t; }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        int wbase = 0, total = 0;
+        for (int w2 = 0; w2 < 8; ++w2) { if (w2 < warp) wbase += warp_tot[w2]; total += warp_tot[w2]; }
+        int run = wbase + incl - local;
+        for (int i = 0; i < per; ++i) {
+            int k = tid * per + i;
+            if (k < len) { int f = flag[k]; flag[k] = run; run += f; }
         }
+        __syncthreads();
+        return total;
+    };
+    for (int k = tid; k < nk; k += 256) {
+        int p = piv_s[k];
+        scan_s[k] = (p >= k1 && slot_of[p - k1] == k) ? 1 : 0;
+    }
+    __syncthreads();
+    const int next = block_scan(scan_s, nk);
+    const int ns = nk + next;
+    for (int k = tid; k < nk; k += 256) {
+        content[k] = (int)(k0 + k);
+        rowof[k] = (int)(k0 + k);
+        int p = piv_s[k];
+        if (p >= k1 && slot_of[p - k1] == k) {
+            content[nk + scan_s[k]] = p;
+            rowof[nk + scan_s[k]] = p;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < nk; k += 256) {
+        int p = piv_s[k];
+        slot_s[k] = (p < k1) ? (int)(p - k0) : nk + scan_s[slot_of[p - k1]];
+    }
+    __syncthreads();
+    // replay the interchanges in order on the slot contents (slot k is final after step k)
+    if (tid == 0) {
         for (int k = 0; k < nk; ++k) {
-            int p = piv_s[k];
-            int sa = k, sb = (p < k1) ? (int)(p - k0) : slot_of[p - k1];
-            int t = content[sa];
-            content[sa] = content[sb];
+            const int sb = slot_s[k];
+            const int t = content[k];
+            content[k] = content[sb];
             content[sb] = t;
         }
-        int c = 0;
-        for (int s = 0; s < ns; ++s) {
-            if (content[s] != rowof[s]) {
-                plan[2 * c] = rowof[s];
-                plan[2 * c + 1] = content[s];
-                ++c;
-            }
-        }
-        *count = c;
     }
+    __syncthreads();
+    // emit the moves dst <- src of the slots whose content changed
+    for (int sidx = tid; sidx < ns; sidx += 256) scan_s[sidx] = (content[sidx] != rowof[sidx]) ? 1 : 0;
+    __syncthreads();
+    const int c = block_scan(scan_s, ns);
+    for (int sidx = tid; sidx < ns; sidx += 256) {
+        if (content[sidx] != rowof[sidx]) {
+            plan[2 * scan_s[sidx]] = rowof[sidx];
+            plan[2 * scan_s[sidx] + 1] = content[sidx];
+        }
+    }
+    if (tid == 0) *count = c;
 }
 
-template <typename T, int CW>
-__global__ void __launch_bounds__(256) k_permute_rows(T* __restrict__ M, int64_t ld, const int* __restrict__ plan,
-                                                      const int* __restrict__ count, int64_t col0, int64_t col1) {
-    extern __shared__ __align__(16) unsigned char prow_raw[];
-    T* buf = reinterpret_cast<T*>(prow_raw);   // [count][CW]
+constexpr int PERM_THREADS = 1024;
+constexpr int PERM_CW = 32;                                   // columns per CTA
+constexpr int PERM_PER = 2 * PERM_MAXK * PERM_CW / PERM_THREADS;  // staged values per thread
+template <typename T>
+__global__ void __launch_bounds__(PERM_THREADS) k_permute_rows(T* __restrict__ M, int64_t ld,
+                                                               const int* __restrict__ plan,
+                                                               const int* __restrict__ count, int64_t col0,
+                                                               int64_t col1) {
+    __shared__ int dst_s[2 * PERM_MAXK], src_s[2 * PERM_MAXK];
     const int cnt = *count;
-    const int64_t c0 = col0 + (int64_t)blockIdx.x * CW;
-    if (c0 >= col1) return;
-    const int width = (int)gmin<int64_t>(CW, col1 - c0);
-    for (int e = threadIdx.x; e < cnt * CW; e += blockDim.x) {
-        int r = e / CW, c = e - r * CW;
-        if (c < width) buf[e] = M[(int64_t)plan[2 * r + 1] * ld + c0 + c];
+    const int64_t c0 = col0 + (int64_t)blockIdx.x * PERM_CW;
+    if (c0 >= col1 || cnt == 0) return;
+    for (int i = threadIdx.x; i < cnt; i += PERM_THREADS) {
+        dst_s[i] = plan[2 * i];
+        src_s[i] = plan[2 * i + 1];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < cnt * CW; e += blockDim.x) {
-        int r = e / CW, c = e - r * CW;
-        if (c < width) M[(int64_t)plan[2 * r] * ld + c0 + c] = buf[e];
-    }
-}
-
-// X = L11^-1 W[r0:r0+w, col0:col1] with L11 the stored unit-lower u_f block at (r0, r0);
-// FP32 substitution; the result is rounded to u_f and written to LU16 (and W).
-// The rounded rows are also written transposed into UT (UT[j * ldut + i], K-major operand).
-template <int WMAX>
-__global__ void __launch_bounds__(256) k_trsm_rows(const uint16_t* __restrict__ LU, int64_t ldl, float* __restrict__ W,
-                                                   int64_t ldw, int64_t r0, int w, int64_t col0, int64_t col1, int fmt,
-                                                   uint16_t* __restrict__ LUout, uint16_t* __restrict__ UT,
-                                                   int64_t ldut) {
-    __shared__ float Ls[WMAX][WMAX];
-    for (int e = threadIdx.x; e < WMAX * WMAX; e += blockDim.x) {
-        int i = e / WMAX, q = e % WMAX;
-        Ls[i][q] = (i < w && q < i) ? uf_to_float(LU[(r0 + i) * ldl + r0 + q], fmt) : 0.0f;
+    const int width = (int)gmin<int64_t>(PERM_CW, col1 - c0);
+    const int c = threadIdx.x % PERM_CW, r0 = threadIdx.x / PERM_CW;
+    constexpr int RSTEP = PERM_THREADS / PERM_CW;
+    T v[PERM_PER];
+    // every source row of this column chunk is read (into registers) before any row is written
+#pragma unroll
+    for (int k = 0; k < PERM_PER; ++k) {
+        const int r = r0 + k * RSTEP;
+        if (r < cnt && c < width) v[k] = M[(int64_t)src_s[r] * ld + c0 + c];
     }
     __syncthreads();
-    const int64_t j = col0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= col1) return;
-    float x[WMAX];
 #pragma unroll
-    for (int i = 0; i < WMAX; ++i) x[i] = (i < w) ? W[(r0 + i) * ldw + j] : 0.0f;
-#pragma unroll
-    for (int i = 1; i < WMAX; ++i) {
-        float acc = x[i];
-#pragma unroll
-        for (int q = 0; q < WMAX; ++q)
-            if (q < i) acc = fmaf(-Ls[i][q], x[q], acc);
-        x[i] = acc;
-    }
-#pragma unroll
-    for (int i = 0; i < WMAX; ++i) {
-        if (i < w) {
-            uint16_t u = float_to_uf(x[i], fmt);
-            LUout[(r0 + i) * ldl + j] = u;
-            W[(r0 + i) * ldw + j] = uf_to_float(u, fmt);
-            if (UT) UT[j * ldut + i] = u;
-        }
+    for (int k = 0; k < PERM_PER; ++k) {
+        const int r = r0 + k * RSTEP;
+        if (r < cnt && c < width) M[(int64_t)dst_s[r] * ld + c0 + c] = v[k];
     }
 }
 
@@ -406,63 +546,122 @@ __global__ void __launch_bounds__(256) k_trsm_rows(const uint16_t* __restrict__ 
 // u_f block (nb <= 256), computed block by block as the per-panel model does: for each 32-row
 // block b, X_b = fl32(L_bb^-1 X_b) by FP32 substitution, U_b = fl_uf(X_b) (stored in LU, UT and
 // used from then on), and the rows below are updated with the u_f operands L[.., b] and U_b
-// (FP32 accumulation). One CTA per 64 columns; L11 and the column slab live in shared memory.
-constexpr int TB_COLS = 64;
+// (FP32 accumulation from zero over the 32 terms, then one FP32 subtraction).
+// One CTA per TBC columns: the column slab lives in shared memory; L11 is staged one 32-column
+// block at a time (double-buffered, the next block fetched into registers during this one).
 constexpr int TB_MAXNB = 256;
+constexpr int TB_LS = 34;   // u16 row stride of a staged L block column
 
-__global__ void __launch_bounds__(256) k_trsm_band(const uint16_t* __restrict__ LU, int64_t ldl, float* __restrict__ W,
-                                                   int64_t ldw, int64_t r0, int nb, int w, int64_t col0, int64_t col1,
-                                                   int fmt, uint16_t* __restrict__ LUout, uint16_t* __restrict__ UT,
-                                                   int64_t ldut) {
+template <int TBC>
+constexpr size_t trsm_band_smem() {
+    return (size_t)TB_MAXNB * (TBC + 1) * sizeof(float) + 2 * (size_t)TB_MAXNB * TB_LS * sizeof(uint16_t);
+}
+
+template <int TBC>
+__global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, int64_t ldl, float* __restrict__ W,
+                                                   int64_t ldw, int64_t r0, int nb, int64_t col0, int64_t col1,
+                                                   int fmt, uint16_t* __restrict__ UT, int64_t ldut) {
+    constexpr int XS = TBC + 1;
+    constexpr int CG = TBC / 4;                 // column groups of 4 in the update
+    constexpr int RG = 256 / CG;                // row groups
+    constexpr int MAXR = (TB_MAXNB - 32 + RG - 1) / RG;
+    constexpr int PF = TB_MAXNB * 32 / 256;     // prefetched L values per thread
     extern __shared__ __align__(16) unsigned char tb_raw[];
-    uint16_t* Ls = reinterpret_cast<uint16_t*>(tb_raw);                            // [nb][nb]
-    float* X = reinterpret_cast<float*>(tb_raw + (size_t)TB_MAXNB * TB_MAXNB * 2); // [nb][TB_COLS + 1]
-    constexpr int XS = TB_COLS + 1;
+    float* X = reinterpret_cast<float*>(tb_raw);                                              // [nb][XS]
+    uint16_t* Lb = reinterpret_cast<uint16_t*>(tb_raw + (size_t)TB_MAXNB * XS * sizeof(float));  // [2][nb][LS]
     const int tid = threadIdx.x;
-    const int64_t c0 = col0 + (int64_t)blockIdx.x * TB_COLS;
-    const int width = (int)gmin<int64_t>(TB_COLS, col1 - c0);
-    for (int e = tid; e < nb * nb; e += 256) {
-        int i = e / nb, q = e - i * nb;
-        Ls[e] = (q < i) ? LU[(r0 + i) * ldl + r0 + q] : (uint16_t)0;
-    }
-    for (int e = tid; e < nb * TB_COLS; e += 256) {
-        int i = e / TB_COLS, c = e - i * TB_COLS;
+    const int64_t c0 = col0 + (int64_t)blockIdx.x * TBC;
+    const int width = (int)gmin<int64_t>(TBC, col1 - c0);
+    for (int e = tid; e < nb * TBC; e += 256) {
+        int i = e / TBC, c = e - i * TBC;
         X[i * XS + c] = (c < width) ? W[(r0 + i) * ldw + c0 + c] : 0.0f;
     }
+    // block column b of L11 (rows b0..nb-1, columns b0..b0+31; zero on and above the diagonal)
+    uint16_t pre[PF];
+    auto fetch = [&](int b0) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int e = tid + k * 256, i = b0 + (e >> 5), q = e & 31;
+            pre[k] = (i < nb && b0 + q < nb && q < i - b0) ? LU[(r0 + i) * ldl + r0 + b0 + q] : (uint16_t)0;
+        }
+    };
+    auto stash = [&](int b0, uint16_t* L) {
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int e = tid + k * 256, i = b0 + (e >> 5), q = e & 31;
+            if (i < nb) L[i * TB_LS + q] = pre[k];
+        }
+    };
+    fetch(0);
+    stash(0, Lb);
     __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += w) {
-        const int wb = min(w, nb - b0);
-        // substitution inside the block: thread per column (FP32 fused updates)
-        if (tid < TB_COLS) {
+    for (int b0 = 0, step = 0; b0 < nb; b0 += 32, ++step) {
+        const int wb = min(32, nb - b0);
+        const uint16_t* L = Lb + (step & 1) * TB_MAXNB * TB_LS;
+        const bool more = b0 + 32 < nb;
+        if (more) fetch(b0 + 32);
+        if (tid < TBC) {
+            // forward substitution in the diagonal block, one thread per column
             const int c = tid;
-            for (int i = 1; i < wb; ++i) {
-                float acc = X[(b0 + i) * XS + c];
-                for (int q = 0; q < i; ++q) acc = fmaf(-uf_to_float(Ls[(b0 + i) * nb + b0 + q], fmt), X[(b0 + q) * XS + c], acc);
-                X[(b0 + i) * XS + c] = acc;
+            float x[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = (i < wb) ? X[(b0 + i) * XS + c] : 0.0f;
+#pragma unroll
+            for (int i = 1; i < 32; ++i) {
+                float acc = x[i];
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (q < i) acc = fmaf(-uf_to_float(L[(b0 + i) * TB_LS + q], fmt), x[q], acc);
+                x[i] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i < wb) {
+                    const uint16_t u = float_to_uf(x[i], fmt);
+                    const float uv = uf_to_float(u, fmt);
+                    X[(b0 + i) * XS + c] = uv;
+                    if (c < width) {
+                        W[(r0 + b0 + i) * ldw + c0 + c] = uv;
+                        LU[(r0 + b0 + i) * ldl + c0 + c] = u;
+                        UT[(c0 + c) * ldut + b0 + i] = u;
+                    }
+                }
             }
         }
         __syncthreads();
-        // round the block to u_f: stored factor, transposed operand, and the value used below
-        for (int e = tid; e < wb * TB_COLS; e += 256) {
-            int i = e / TB_COLS, c = e - i * TB_COLS;
-            uint16_t u = float_to_uf(X[(b0 + i) * XS + c], fmt);
-            float uv = uf_to_float(u, fmt);
-            X[(b0 + i) * XS + c] = uv;
-            if (c < width) {
-                LUout[(r0 + b0 + i) * ldl + c0 + c] = u;
-                W[(r0 + b0 + i) * ldw + c0 + c] = uv;
-                UT[(c0 + c) * ldut + b0 + i] = u;
+        // rows below the block: X[i] -= sum_q L[i, b0+q] U_b[q]
+        const int rb = b0 + wb;
+        if (rb < nb) {
+            const int tx = tid % CG, ty = tid / CG;
+            float acc[MAXR][4];
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
+            for (int q = 0; q < wb; ++q) {
+                float u[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) u[k] = X[(b0 + q) * XS + tx * 4 + k];
+#pragma unroll
+                for (int m = 0; m < MAXR; ++m) {
+                    const int i = rb + ty + m * RG;
+                    if (i < nb) {
+                        const float l = uf_to_float(L[i * TB_LS + q], fmt);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) acc[m][k] = fmaf(l, u[k], acc[m][k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m) {
+                const int i = rb + ty + m * RG;
+                if (i < nb) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) X[i * XS + tx * 4 + k] -= acc[m][k];
+                }
             }
         }
-        __syncthreads();
-        // rows below the block: X[i] -= L[i, b0:b0+wb] U_b
-        const int rows_below = nb - (b0 + wb);
-        for (int e = tid; e < rows_below * TB_COLS; e += 256) {
-            int i = b0 + wb + e / TB_COLS, c = e % TB_COLS;
-            float acc = 0.0f;
-            for (int q = 0; q < wb; ++q) acc = fmaf(uf_to_float(Ls[i * nb + b0 + q], fmt), X[(b0 + q) * XS + c], acc);
-            X[i * XS + c] -= acc;
-        }
+        if (more) stash(b0 + 32, Lb + ((step + 1) & 1) * TB_MAXNB * TB_LS);
         __syncthreads();
     }
 }
@@ -571,39 +770,37 @@ static gir_status make_plan(const int* ipiv, int64_t k0, int64_t k1, int64_t n, 
     return GIR_OK;
 }
 
-static gir_status permute_f32(float* W, int64_t ldw, int64_t col0, int64_t col1, int64_t maxrows, const SwapScratch& sw,
-                              cudaStream_t s) {
+template <typename T>
+static gir_status permute_rows(T* M, int64_t ld, int64_t col0, int64_t col1, const SwapScratch& sw, cudaStream_t s) {
     if (col1 <= col0) return GIR_OK;
-    constexpr int CW = 32;
-    size_t smem = (size_t)maxrows * CW * sizeof(float);
-    count_launch(), k_permute_rows<float, CW><<<(unsigned)((col1 - col0 + CW - 1) / CW), 256, smem, s>>>(
-        W, ldw, sw.plan, sw.count, col0, col1);
-    GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
-}
-
-static gir_status permute_u16(uint16_t* LU, int64_t ldl, int64_t col0, int64_t col1, int64_t maxrows,
-                              const SwapScratch& sw, cudaStream_t s) {
-    if (col1 <= col0) return GIR_OK;
-    constexpr int CW = 64;
-    size_t smem = (size_t)maxrows * CW * sizeof(uint16_t);
-    count_launch(), k_permute_rows<uint16_t, CW><<<(unsigned)((col1 - col0 + CW - 1) / CW), 256, smem, s>>>(
-        LU, ldl, sw.plan, sw.count, col0, col1);
+    count_launch(), k_permute_rows<T><<<(unsigned)((col1 - col0 + PERM_CW - 1) / PERM_CW), PERM_THREADS, 0, s>>>(
+        M, ld, sw.plan, sw.count, col0, col1);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
 
 static gir_status launch_panel(float* W, int64_t ldw, int64_t c0, int64_t n, int wc, int* ipiv, int* flags,
-                               const LUPlan& plan, cudaStream_t s) {
+                               const LUPlan& plan, const PanelTail& tail, cudaStream_t s) {
     const int64_t h = n - c0;
-    // cluster size: smallest C such that the panel fits the shared-memory budget per CTA
     const int64_t budget = plan.panel_smem_budget;
     const int WC = plan.w;
     int64_t bytes_per_row = (int64_t)(WC + 1) * 4;  // padded rows (see k_panel)
+    // cluster size: enough CTAs for the panel to fit the shared-memory budget, and (where the
+    // cluster limit allows) at most two rows per thread
     int C = (int)((h * bytes_per_row + budget - 1) / budget);
     if (C < 1) C = 1;
     if (C > plan.max_cluster) return GIR_UNSUPPORTED;
+    if (!plan.forced_cluster) {
+        int64_t by_rows = (h + 2 * PANEL_THREADS - 1) / (2 * PANEL_THREADS);
+        C = (int)gmax<int64_t>(C, gmin<int64_t>(by_rows, plan.max_cluster));
+    }
     int rpc = (int)((h + C - 1) / C);
+    while (!plan.forced_cluster && (int64_t)rpc * bytes_per_row > budget && C < plan.max_cluster) {
+        ++C;
+        rpc = (int)((h + C - 1) / C);
+    }
+    if ((int64_t)rpc * bytes_per_row > (plan.forced_cluster ? LUPlan().panel_smem_budget : budget))
+        return GIR_UNSUPPORTED;
     size_t smem = (WC == 32 ? sizeof(PanelShared<32>) : sizeof(PanelShared<16>)) + (size_t)rpc * bytes_per_row;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
@@ -619,9 +816,9 @@ static gir_status launch_panel(float* W, int64_t ldw, int64_t c0, int64_t n, int
     cfg.numAttrs = 1;
     count_launch();
     if (WC == 32) {
-        GIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel<32>, W, ldw, c0, n, wc, rpc, ipiv, flags));
+        GIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel<32>, W, ldw, c0, n, wc, rpc, ipiv, flags, tail));
     } else {
-        GIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel<16>, W, ldw, c0, n, wc, rpc, ipiv, flags));
+        GIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel<16>, W, ldw, c0, n, wc, rpc, ipiv, flags, tail));
     }
     return GIR_OK;
 }
@@ -637,8 +834,10 @@ gir_status lu_panel_only(float* W, int64_t ldw, int64_t m, int w, int* ipiv, int
         int64_t bytes = m * (int64_t)(plan.w + 1) * 4;
         plan.panel_smem_budget = (bytes + cluster - 1) / cluster;
         if (plan.panel_smem_budget < 4) plan.panel_smem_budget = 4;
+        plan.forced_cluster = 1;
     }
-    return launch_panel(W, ldw, 0, m, w, ipiv, flags, plan, s);
+    PanelTail tail = {nullptr, 0, 0, 0, 0, 0, 0, nullptr, 0};
+    return launch_panel(W, ldw, 0, m, w, ipiv, flags, plan, tail, s);
 }
 
 gir_status lu_update_only(float* C, int64_t ldc, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
@@ -652,21 +851,17 @@ gir_status lu_update_only(float* C, int64_t ldc, const uint16_t* A, int64_t lda,
 gir_status lu_prepare(LUPlan& plan) {
     int dev;
     GIR_CUDA_TRY(cudaGetDevice(&dev));
-    const size_t max_smem = 200 * 1024;
+    const size_t max_smem = sizeof(PanelShared<32>) + (size_t)plan.panel_smem_budget;
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    plan.panel_smem_budget = 160 * 1024;
-    plan.max_cluster = 16;
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      TB_MAXNB * TB_MAXNB * 2 + TB_MAXNB * (TB_COLS + 1) * 4));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_band_smem<16>()));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_band_smem<64>()));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_swap_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(PERM_MAXN * sizeof(int))));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_permute_rows<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * PERM_MAXK * 32 * (int)sizeof(float)));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_permute_rows<uint16_t, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * PERM_MAXK * 64 * (int)sizeof(uint16_t)));
     const char* e = getenv("GIR_NO_TC");
     if (e && e[0] == '1') plan.use_tc = 0;  // CUDA-core trailing update (for A/B comparisons)
     return GIR_OK;
@@ -700,67 +895,71 @@ gir_status lu_scale_quantize(const double* A, int64_t n, int64_t lda, int uf, do
 // block's panels (a few SMs) are factored. Events keep every W update, row interchange and
 // UT access ordered: (b)_k finishes before block k+1's end-of-block interchanges and (a)_{k+1}.
 gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv, int64_t n, int fmt,
-                     const LUPlan& plan, uint16_t* UT, int* flags, cudaStream_t s) {
+                     const LUPlan& plan, uint16_t* UT, int* flags, cudaStream_t s_user) {
     const int w = plan.w;
     const int NB = plan.nb;
     const int64_t ldut = NB;
     if (NB > PERM_MAXK || NB > TB_MAXNB) return GIR_UNSUPPORTED;
     SwapScratch sw;
-    // side stream and events, released on every return path (work still queued completes first)
-    struct Side {
-        cudaStream_t s2 = nullptr;
-        cudaEvent_t ev_swapped = nullptr, ev_b = nullptr;
-        ~Side() {
+    // The critical path (panels, interchanges, next-block update) runs on a highest-priority
+    // stream so that its small kernels get SMs ahead of the side stream's bulk trailing update.
+    // Streams and events are released on every return path (queued work completes first).
+    struct Streams {
+        cudaStream_t s = nullptr, s2 = nullptr;
+        cudaEvent_t ev_swapped = nullptr, ev_b = nullptr, ev_io = nullptr;
+        ~Streams() {
             if (ev_swapped) cudaEventDestroy(ev_swapped);
             if (ev_b) cudaEventDestroy(ev_b);
+            if (ev_io) cudaEventDestroy(ev_io);
             if (s2) cudaStreamDestroy(s2);
+            if (s) cudaStreamDestroy(s);
         }
-    } side;
-    cudaStream_t& s2 = side.s2;
-    cudaEvent_t& ev_swapped = side.ev_swapped;
-    cudaEvent_t& ev_b = side.ev_b;
-    GIR_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
-    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ev_swapped, cudaEventDisableTiming));
-    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming));
+    } ss_;
+    int prio_least = 0, prio_greatest = 0;
+    GIR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    GIR_CUDA_TRY(cudaStreamCreateWithPriority(&ss_.s, cudaStreamNonBlocking, prio_greatest));
+    GIR_CUDA_TRY(cudaStreamCreateWithPriority(&ss_.s2, cudaStreamNonBlocking, prio_least));
+    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ss_.ev_swapped, cudaEventDisableTiming));
+    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ss_.ev_b, cudaEventDisableTiming));
+    GIR_CUDA_TRY(cudaEventCreateWithFlags(&ss_.ev_io, cudaEventDisableTiming));
+    cudaStream_t s = ss_.s;
+    cudaStream_t s2 = ss_.s2;
+    cudaEvent_t ev_swapped = ss_.ev_swapped, ev_b = ss_.ev_b;
+    // join: the factorization starts after the caller's earlier work and ends before its later work
+    GIR_CUDA_TRY(cudaEventRecord(ss_.ev_io, s_user));
+    GIR_CUDA_TRY(cudaStreamWaitEvent(s, ss_.ev_io, 0));
     GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.plan), 4 * PERM_MAXK * sizeof(int), s));
     GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.count), sizeof(int), s));
     bool b_pending = false;  // a (b) part is running on s2
     gir_status st = GIR_OK;
-    auto trsm_band = [&](int64_t C0, int64_t NBc, int64_t col0, int64_t col1, cudaStream_t ss) {
+    // wide column slabs for the bulk (two CTAs per SM), narrow ones for the next block's 256
+    // columns on the critical path (16 CTAs)
+    auto trsm_band = [&](int64_t C0, int64_t NBc, int64_t col0, int64_t col1, bool narrow, cudaStream_t ss) {
         if (col1 <= col0) return;
-        const size_t smem = (size_t)TB_MAXNB * TB_MAXNB * 2 + (size_t)NBc * (TB_COLS + 1) * 4;
-        count_launch(), k_trsm_band<<<(unsigned)((col1 - col0 + TB_COLS - 1) / TB_COLS), 256, smem, ss>>>(
-            LU, ldl, W, ldw, C0, (int)NBc, w, col0, col1, fmt, LU, UT, ldut);
+        if (narrow) {
+            count_launch(), k_trsm_band<16><<<(unsigned)((col1 - col0 + 15) / 16), 256, trsm_band_smem<16>(), ss>>>(
+                LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
+        } else {
+            count_launch(), k_trsm_band<64><<<(unsigned)((col1 - col0 + 63) / 64), 256, trsm_band_smem<64>(), ss>>>(
+                LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
+        }
     };
     for (int64_t C0 = 0; C0 < n && st == GIR_OK; C0 += NB) {
         const int64_t NBc = gmin<int64_t>(NB, n - C0);
         const int64_t Cend = C0 + NBc;
         for (int64_t c0 = C0; c0 < Cend; c0 += w) {
             const int wc = (int)gmin<int64_t>(w, Cend - c0);
-            {
-                int t_ = trace_begin(s);
-                GIR_TRY(launch_panel(W, ldw, c0, n, wc, ipiv, flags, plan, s));
-                trace_end(t_, "lu panel", s);
-            }
-            GIR_TRY(debug_check("panel", C0, c0, flags, s));
             int t_ = trace_begin(s);
             {
-                int64_t tot = (n - c0) * wc;
-                int g = (int)gmin<int64_t>((tot + 255) / 256, 152 * 8);
-                count_launch(), k_store_panel<<<g, 256, 0, s>>>(W, ldw, LU, ldl, c0, wc, n, fmt);
+                // the panel kernel also stores the u_f panel, applies its interchanges to the
+                // block's later columns of W and earlier columns of LU, and solves for U12
+                PanelTail tail = {LU, ldl, fmt, c0 + wc, Cend, C0, c0, UT + (c0 - C0), ldut};
+                GIR_TRY(launch_panel(W, ldw, c0, n, wc, ipiv, flags, plan, tail, s));
             }
-            GIR_TRY(make_plan(ipiv, c0, c0 + wc, n, sw, s));
-            GIR_TRY(permute_f32(W, ldw, c0 + wc, Cend, 2 * wc, sw, s));
-            GIR_TRY(permute_u16(LU, ldl, C0, c0, 2 * wc, sw, s));
-            trace_end(t_, "lu store+swaps", s);
+            trace_end(t_, "lu panel", s);
+            GIR_TRY(debug_check("panel", C0, c0, flags, s));
             if (c0 + wc < Cend) {
                 int64_t ncols = Cend - (c0 + wc);
-                t_ = trace_begin(s);
-                count_launch(), k_trsm_rows<32><<<(unsigned)((ncols + 255) / 256), 256, 0, s>>>(LU, ldl, W, ldw, c0, wc,
-                                                                                                 c0 + wc, Cend, fmt, LU,
-                                                                                                 UT + (c0 - C0), ldut);
-                trace_end(t_, "lu inner trsm", s);
-                GIR_TRY(debug_check("inner trsm", C0, c0, flags, s));
                 t_ = trace_begin(s);
                 GIR_TRY(gemm_sub(W + (c0 + wc) * ldw + (c0 + wc), ldw, LU + (c0 + wc) * ldl + c0, ldl,
                                  LU + c0 * ldl + (c0 + wc), ldl, UT + (c0 + wc) * ldut + (c0 - C0), ldut,
@@ -777,15 +976,15 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
         }
         int t_ = trace_begin(s);
         GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, s));
-        GIR_TRY(permute_f32(W, ldw, Cend, n, 2 * NBc, sw, s));
-        GIR_TRY(permute_u16(LU, ldl, 0, C0, 2 * NBc, sw, s));
+        GIR_TRY(permute_rows<float>(W, ldw, Cend, n, sw, s));
+        GIR_TRY(permute_rows<uint16_t>(LU, ldl, 0, C0, sw, s));
         trace_end(t_, "lu outer swaps", s);
         if (Cend < n) {
             const int64_t ntr = n - Cend;
             const int64_t Ca = gmin<int64_t>(n, Cend + NB);  // (a): columns [Cend, Ca)
             // (a) on the main stream: the next block's columns
             t_ = trace_begin(s);
-            trsm_band(C0, NBc, Cend, Ca, s);
+            trsm_band(C0, NBc, Cend, Ca, true, s);
             trace_end(t_, "lu outer trsm", s);
             GIR_TRY(debug_check("outer trsm a", C0, Cend, flags, s));
             t_ = trace_begin(s);
@@ -797,7 +996,7 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 GIR_CUDA_TRY(cudaEventRecord(ev_swapped, s));
                 GIR_CUDA_TRY(cudaStreamWaitEvent(s2, ev_swapped, 0));
                 int tb = trace_begin(s2);
-                trsm_band(C0, NBc, Ca, n, s2);
+                trsm_band(C0, NBc, Ca, n, false, s2);
                 trace_end(tb, "lu outer trsm", s2);
                 tb = trace_begin(s2);
                 GIR_TRY(gemm_sub(W + Cend * ldw + Ca, ldw, LU + Cend * ldl + C0, ldl, LU + C0 * ldl + Ca, ldl,
@@ -812,6 +1011,8 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
     if (b_pending) GIR_CUDA_TRY(cudaStreamWaitEvent(s, ev_b, 0));
     cudaFreeAsync(sw.plan, s);
     cudaFreeAsync(sw.count, s);
+    GIR_CUDA_TRY(cudaEventRecord(ss_.ev_io, s));
+    GIR_CUDA_TRY(cudaStreamWaitEvent(s_user, ss_.ev_io, 0));
     GIR_CUDA_TRY(cudaGetLastError());
     return st;
 }

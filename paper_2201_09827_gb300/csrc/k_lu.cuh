@@ -7,16 +7,10 @@ namespace gir {
 struct LUPlan {
     int w = 32;                       // panel width (one cluster factors w columns)
     int nb = 256;                     // outer block width (K of the big trailing update)
-    int use_tc = 1;                   // Test hooks: one panel factorization of an m x w FP32 block (rows 0..m) with a forced
-// cluster size (0 = automatic), and one trailing update through the chosen path.
-gir_status lu_panel_only(float* W, int64_t ldw, int64_t m, int w, int* ipiv, int cluster, int* flags, cudaStream_t s);
-gir_status lu_update_only(float* C, int64_t ldc, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
-                          const uint16_t* Bt, int64_t ldbt, int64_t M, int64_t N, int64_t K, int fmt, int use_tc,
-                          int* flags, cudaStream_t s);
-
-// tcgen05 trailing update when the shape allows it
-    int64_t panel_smem_budget = 160 * 1024;
-    int max_cluster = 16;
+    int use_tc = 1;                   // tcgen05 trailing update when the shape allows it
+    int64_t panel_smem_budget = 200 * 1024;  // panel rows held per CTA, bytes
+    int max_cluster = 16;             // CTAs per panel cluster (non-portable size)
+    int forced_cluster = 0;           // test hook: cluster size fixed by the budget alone
 };
 
 gir_status lu_prepare(LUPlan& plan);
