@@ -100,7 +100,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(n_s=2048, kappa=1e2, uf="bf16"):
+def oracle_sample(n_s=3072, kappa=1e2, uf="bf16"):
     """The CPU oracle (as it stands) on one system of the benchmark family at size n_s."""
     import numpy as np
     from oracle.ir import Params as OP, solve as osolve
@@ -154,36 +154,71 @@ def config_json(args, world):
             "l2": "inputs larger than L2 (A is 8n^2 bytes = 2.15 GB at n=16384)"}
 
 
-# algorithmic bytes / flops per launch of the phases the trace reports
-def roofline_for(phase, total_ms, calls, args, peaks, peak_kind):
-    n = args.n
+# Algorithmic work of the traced kernels: per-unit figures times the units of all launches of
+# the step (the per-launch figure is the total over the step divided by the launch count).
+FP32_ALU_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def phase_work(phase, args, calls):
+    """(total algorithmic units over all launches of the step, unit, bound) or None."""
+    n, nb, w = args.n, 256, 32
+    steps = max(1, args.steps)
+    if phase == "lu panel":
+        # read the FP32 panel, write it back and its u_f copy: 10 bytes per panel entry
+        tot = sum(10.0 * (n - c0) * min(w, n - c0) for c0 in range(0, n, w))
+        return steps * tot, "GB/s", "hbm"
+    if phase == "trsv":
+        # one triangle of the 16-bit factors (n^2 / 2 entries) plus the right-hand side and result
+        return calls * (1.0 * n * n + 24.0 * n), "GB/s", "hbm"
     if phase == "gemv":
-        per = 8.0 * n * n + 16.0 * n
-        unit, bound, pk = "GB/s", "hbm", peaks["hbm_gbs"]
-        achieved = per / ((total_ms / calls) * 1e-3) / 1e9
-    elif phase == "minv":
-        per = 2.0 * n * n + 48.0 * n          # L and U (16-bit, n^2 entries in all) + vectors
-        unit, bound, pk = "GB/s", "hbm", peaks["hbm_gbs"]
-        achieved = per / ((total_ms / calls) * 1e-3) / 1e9
-    elif phase == "residual":
-        per = 8.0 * n * n + 24.0 * n
-        unit, bound, pk = "GB/s", "hbm", peaks["hbm_gbs"]
-        achieved = per / ((total_ms / calls) * 1e-3) / 1e9
-    elif phase == "lu outer gemm":
-        nb = 256
-        fl = 0.0
-        c = nb
-        while c < n:
-            fl += 2.0 * (n - c) * (n - c) * nb
-            c += nb
-        per = fl / max(calls, 1)
-        unit, bound, pk = "TFLOP/s", "tensor", peaks["bf16_tflops"]
-        achieved = per / ((total_ms / calls) * 1e-3) / 1e12
-    else:
+        return calls * (8.0 * n * n + 16.0 * n), "GB/s", "hbm"
+    if phase == "residual":
+        return calls * (8.0 * n * n + 24.0 * n), "GB/s", "hbm"
+    if phase == "lu outer gemm":
+        tot = sum(2.0 * (n - c) * (n - c) * nb for c in range(nb, n, nb))
+        return steps * tot, "TFLOP/s", "tensor"
+    if phase == "lu outer trsm":
+        # FP32 substitution of the U12 band: nb^2 fused multiply-adds per trailing column
+        tot = sum(2.0 * nb * nb / 2 * (n - c) for c in range(nb, n, nb))
+        return steps * tot, "TFLOP/s", "alu"
+    return None
+
+
+def read_traffic(kernel_phase):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel's source
+    changed since the capture (the summary records a hash of the file)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
         return None
-    return {"kernel": phase, "bound": bound, "achieved": achieved, "peak": pk, "unit": unit,
-            "frac": achieved / pk, "traffic": None, "peak_source": peak_kind,
-            "per_launch": per, "launches": calls, "avg_ms": total_ms / calls}
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0].replace("_", " ") == kernel_phase:
+            src = os.path.join(ROOT, "paper_2201_09827_gb300", "csrc", parts[2])
+            try:
+                h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            except OSError:
+                return None
+            return float(parts[1]) if h == parts[3] else None
+    return None
+
+
+def roofline_for(phase, total_ms, calls, args, peaks, peak_kind):
+    work = phase_work(phase, args, calls)
+    if work is None:
+        return None
+    tot, unit, bound = work
+    per = tot / max(calls, 1)
+    avg_s = (total_ms / calls) * 1e-3
+    if unit == "GB/s":
+        achieved, pk, pk_src = per / avg_s / 1e9, peaks["hbm_gbs"], f"hbm_gbs of {peak_kind}"
+    elif bound == "tensor":
+        achieved, pk, pk_src = per / avg_s / 1e12, peaks["bf16_tflops"], f"bf16_tflops (burst) of {peak_kind}"
+    else:
+        achieved, pk, pk_src = per / avg_s / 1e12, FP32_ALU_TFLOPS_DERIVED, "derived FP32 FMA peak"
+    return {"kernel": phase, "bound": bound, "achieved": achieved, "peak": pk, "unit": unit, "frac": achieved / pk,
+            "traffic": read_traffic(phase), "peak_source": pk_src, "per_launch": per, "launches": calls,
+            "avg_ms": total_ms / calls}
 
 
 def main():
@@ -197,7 +232,7 @@ def main():
     ap.add_argument("--uf", default="bf16")
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--k", type=int, default=10)
-    ap.add_argument("--sample-n", type=int, default=2048)
+    ap.add_argument("--sample-n", type=int, default=3072)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-lu", action="store_true")
@@ -274,32 +309,26 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = t.item()
 
-    # ---------------- end to end through the C ABI with host buffers ----------------
+    # ---------------- end to end through the public API with host buffers ----------------
+    # gir.solve with pinned CPU tensors: H2D of A and b, factor + solve, D2H of x, per step
     e2e = None
     if not args.no_e2e:
         Ah = A.cpu().pin_memory()
         bh = b.cpu().pin_memory()
-        xh = torch.empty(n, dtype=torch.float64).pin_memory()
-        Ad = torch.empty_like(A)
-        bd = torch.empty_like(b)
-        xd = torch.empty_like(b)
         et = []
         for it in range(max(2, args.steps // 2) + 1):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            Ad.copy_(Ah, non_blocking=True)
-            bd.copy_(bh, non_blocking=True)
-            step(Ad, bd, xd)
-            xh.copy_(xd, non_blocking=True)
+            xh, _ = gir.solve(Ah, bh, prm)
             e1.record(stream)
             e1.synchronize()
             if it > 0:
                 et.append(e0.elapsed_time(e1))
         e2e = {"value": statistics.median(et), "unit": "ms", "h2d_bytes_per_step": 8 * n * n + 8 * n,
-               "d2h_bytes_per_step": 8 * n}
-        del Ad, bd, xd, Ah
+               "d2h_bytes_per_step": 8 * n, "api": "paper_2201_09827_gb300.solve(A_host_pinned, b_host_pinned)"}
+        del Ah, bh
 
     # ---------------- FP64 LU comparator on the same GPU (library, context) ----------------
     fp64_lu_ms = None
@@ -314,13 +343,18 @@ def main():
         fp64_lu_ms = e0.elapsed_time(e1)
         del xl
 
-    # ---------------- roofline of the dominant phase ----------------
-    roof = None
+    # ---------------- roofline of the dominant kernel ----------------
+    # Phases are kernel launches timed by CUDA events on their own streams inside the library;
+    # "minv" and "cycle close" wrap several kernels and are not candidates.
+    roof, others = None, []
     if trace:
-        known = {k: v for k, v in trace.items() if k in ("gemv", "minv", "residual", "lu outer gemm")}
-        if known:
-            dom = max(known, key=lambda k: known[k][0])
-            roof = roofline_for(dom, known[dom][0], known[dom][1], args, peaks, peak_kind)
+        cands = sorted(((v[0], k) for k, v in trace.items() if phase_work(k, args, v[1]) is not None), reverse=True)
+        for i, (tot, k) in enumerate(cands[:4]):
+            r = roofline_for(k, trace[k][0], trace[k][1], args, peaks, peak_kind)
+            if i == 0:
+                roof = r
+            else:
+                others.append(r)
     phase_ms = {k: round(v[0] / args.steps, 3) for k, v in sorted(trace.items(), key=lambda kv: -kv[1][0])}
 
     cpu = None
@@ -336,7 +370,7 @@ def main():
                "result": {"status": last.status, "its": last.its, "total_its": last.total_its,
                           "ir_steps": last.ir_steps, "berr_dd": eta, "ms_factor": last.ms_factor,
                           "ms_solve": last.ms_solve, "times_ms": times},
-               "fp64_lu_ms": fp64_lu_ms, "phase_ms_per_step": phase_ms}
+               "fp64_lu_ms": fp64_lu_ms, "phase_ms_per_step": phase_ms, "roofline_next": others}
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -4,6 +4,6 @@ The solver (Algorithms 2-4 of Oktay & Carson, arXiv 2201.09827) is the CUDA libr
 ``libgir.so`` behind the C ABI in ``include/gir.h``; ``gir`` is its thin ctypes binding.
 """
 from .gir import (  # noqa: F401
-    Params, Info, Factorization, GirSolve, GirError, residual, gemv, small_eig, batch_solve, load, lu_panel, lu_update, trace_enable, trace_report, launch_count,
+    Params, Info, Factorization, GirSolve, GirError, solve, residual, gemv, small_eig, batch_solve, load, lu_panel, lu_update, trace_enable, trace_report, launch_count,
     library_path,
 )

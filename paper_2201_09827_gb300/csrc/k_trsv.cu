@@ -9,6 +9,7 @@
 // deadlock; every wait is bounded and a timeout sets an abort flag that releases all waiters.
 #include "gir_internal.cuh"
 #include "k_trsv.cuh"
+#include "trace.cuh"
 
 namespace gir {
 
@@ -314,8 +315,10 @@ static gir_status run_trsv(TrsvState& st, const float2* D, const double* z64, co
     st.tickets += (unsigned long long)st.nblk;
     int epoch = ++st.epoch;
     GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
+    const int tslot = trace_begin(s);
     count_launch(), k_trsv<LOWER, TRANS><<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, st.nblk, z64, zff, y, ready,
                                                  st.ticket_ctr, base, epoch, st.abort_flag, flags);
+    trace_end(tslot, "trsv", s);
     st.calls++;
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;

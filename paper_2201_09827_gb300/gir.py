@@ -359,6 +359,35 @@ def launch_count() -> int:
     return int(load().gir_launch_count())
 
 
+def solve(A, b, params: Params | None = None, stream=None):
+    """x = A^-1 b by RGMRES-IR (Algorithm 4) on one system.
+
+    A and b may be CUDA tensors (the solve runs in place on the device) or CPU tensors: then
+    they are staged through pinned host buffers, copied to the current device on the solve's
+    stream, and x is copied back to a CPU tensor (the host <-> device copies are part of the
+    call). Returns (x, Info)."""
+    params = params or Params()
+    host = not A.is_cuda
+    if host:
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            Ah = A if A.is_pinned() else A.pin_memory()
+            bh = b if b.is_pinned() else b.pin_memory()
+            Ad = Ah.to("cuda", non_blocking=True)
+            bd = bh.to("cuda", non_blocking=True)
+            F = Factorization(Ad, params, stream=s)
+            xd, info = F.solve(Ad, bd, stream=s)
+            F.close()
+            xh = torch.empty(xd.shape, dtype=xd.dtype, pin_memory=True)
+            xh.copy_(xd, non_blocking=True)
+        s.synchronize()
+        return xh, info
+    F = Factorization(A, params, stream=stream)
+    x, info = F.solve(A, b, stream=stream)
+    F.close()
+    return x, info
+
+
 def batch_solve(As, bs, params: Params, stream=None):
     lib = load()
     nsys = len(As)
