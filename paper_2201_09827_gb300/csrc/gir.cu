@@ -95,14 +95,46 @@ gir_status dalloc_t(T** p, size_t count) {
     return dalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
+// Handles and factorization temporaries come from the device's stream-ordered pool, which is
+// told to keep freed memory (release threshold = max) so that repeated factorizations reuse
+// it without going back to the driver.
+gir_status pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    static int configured_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_dev != dev) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+        configured_dev = dev;
+    }
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return (e == cudaErrorMemoryAllocation) ? GIR_OOM : GIR_CUDA_ERROR;
+    }
+    return GIR_OK;
+}
+
+template <typename T>
+gir_status pool_alloc_t(T** p, size_t count, cudaStream_t s) {
+    return pool_alloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
 void free_handle(gir_handle* h) {
     if (!h) return;
+    cudaDeviceSynchronize();   // no kernel of any stream may still use the handle's memory
     void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.perm, h->trsv.z, h->trsv.y1,
                     h->trsv.y2, h->trsv.ready, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
                     h->scratch, h->st, h->qh, h->dsc, h->dflags};
+    // pool memory: every use is finished (callers synchronise the device first)
     for (void* q : ptrs)
-        if (q) cudaFree(q);
+        if (q) cudaFreeAsync(q, 0);
     if (h->hsc) cudaFreeHost(h->hsc);
     if (h->hst) cudaFreeHost(h->hst);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -563,10 +595,10 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     h->scaled = (params->uf == GIR_FP16);
     cudaGetDevice(&h->dev);
     gir_status st = GIR_OK;
-#define ALLOC(ptr, cnt)                                   \
-    do {                                                  \
-        st = dalloc_t(&(ptr), (size_t)(cnt));             \
-        if (st != GIR_OK) { free_handle(h); return st; }  \
+#define ALLOC(ptr, cnt)                                                             \
+    do {                                                                            \
+        st = pool_alloc_t(&(ptr), (size_t)(cnt), s);                                \
+        if (st != GIR_OK) { free_handle(h); return st; }                            \
     } while (0)
     h->ldl = (n + 7) / 8 * 8;
     const int64_t ldw = (n + 7) / 8 * 8;
@@ -602,7 +634,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     ALLOC(h->scratch, h->scratch_len);
     {
         void* p = nullptr;
-        st = dalloc(&p, sizeof(SmallState));
+        st = pool_alloc(&p, sizeof(SmallState), s);
         if (st != GIR_OK) { free_handle(h); return st; }
         h->st = reinterpret_cast<SmallState*>(p);
     }
@@ -625,12 +657,13 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     uint16_t* UT = nullptr;
     st = lu_prepare(h->plan);
     if (params->lu_nb > 0) h->plan.nb = (params->lu_nb + h->plan.w - 1) / h->plan.w * h->plan.w;
-    if (st == GIR_OK) st = dalloc_t(&W, (size_t)n * ldw);
-    if (st == GIR_OK) st = dalloc_t(&colmax, (size_t)n);
-    if (st == GIR_OK) st = dalloc_t(&UT, (size_t)n * h->plan.nb + 64);
+    if (st == GIR_OK) st = pool_alloc_t(&W, (size_t)n * ldw, s);
+    if (st == GIR_OK) st = pool_alloc_t(&colmax, (size_t)n, s);
+    if (st == GIR_OK) st = pool_alloc_t(&UT, (size_t)n * h->plan.nb + 64, s);
     if (st != GIR_OK) {
-        if (W) cudaFree(W);
-        if (colmax) cudaFree(colmax);
+        if (W) cudaFreeAsync(W, s);
+        if (colmax) cudaFreeAsync(colmax, s);
+        if (UT) cudaFreeAsync(UT, s);
         free_handle(h);
         return st;
     }
@@ -647,15 +680,16 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
         st = lu_scale_quantize(A, n, lda, params->uf, h->R, h->S, &mu, W, ldw, colmax, h->dflags, s);
         h->mu = mu;
     }
-    if (st == GIR_OK) st = lu_factor(W, ldw, h->LU, h->ldl, h->ipiv, n, h->fmt, h->plan, UT, h->dflags, s);
-    if (st == GIR_OK) st = trsv_setup(h->trsv, h->LU, h->ldl, n, h->fmt, h->ipiv, s);
+    if (st == GIR_OK)
+        st = lu_factor(W, ldw, h->LU, h->ldl, h->ipiv, h->trsv.perm, n, h->fmt, h->plan, UT, h->dflags, s);
+    if (st == GIR_OK) st = trsv_setup(h->trsv, h->LU, h->ldl, n, h->fmt, s);
+    cudaFreeAsync(W, s);
+    cudaFreeAsync(colmax, s);
+    cudaFreeAsync(UT, s);
     cudaEventRecord(h->ev1, s);
     cudaEventSynchronize(h->ev1);
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    cudaFree(W);
-    cudaFree(colmax);
-    cudaFree(UT);
     if (st == GIR_OK) {
         int f = read_flags(h, s);
         st = flags_status(f);

@@ -65,15 +65,29 @@ __global__ void k_col_scale(const unsigned long long* __restrict__ colmax, int64
 __global__ void __launch_bounds__(256) k_quantize(const double* __restrict__ A, int64_t n, int64_t lda,
                                                   const double* __restrict__ R, const double* __restrict__ S,
                                                   double mu, float* __restrict__ W, int64_t ldw, int* flags) {
-    const int64_t total = n * n;
+    // rows in a grid-stride loop, columns by the CTA's threads (two per thread with 16-byte loads
+    // where both row pitches and base addresses allow)
     bool bad = false;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = e / n, j = e - i * n;
-        double v = A[i * lda + j];
+    const bool vec = ((lda & 1) == 0) && ((ldw & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(W) & 7) == 0);
+    auto cvt = [&](double v, int64_t i, int64_t j) {
         if (R) v *= R[i] * S[j] * mu;
-        float f = __double2float_rn(v);
+        const float f = __double2float_rn(v);
         bad |= !(fabsf(f) <= 3.4028234663852886e38f);
-        W[i * ldw + j] = f;
+        return f;
+    };
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const double* a = A + i * lda;
+        float* w = W + i * ldw;
+        if (vec) {
+            for (int64_t j = 2 * (int64_t)threadIdx.x; j + 1 < n; j += 2 * (int64_t)blockDim.x) {
+                const double2 v = *reinterpret_cast<const double2*>(a + j);
+                *reinterpret_cast<float2*>(w + j) = make_float2(cvt(v.x, i, j), cvt(v.y, i, j + 1));
+            }
+            if ((n & 1) && threadIdx.x == 0) w[n - 1] = cvt(a[n - 1], i, n - 1);
+        } else {
+            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) w[j] = cvt(a[j], i, j);
+        }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, DEV_NONFINITE);
 }
@@ -112,19 +126,58 @@ __device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
     asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+constexpr long long PANEL_WAIT_LIMIT = 4000000LL;   // polls of one column's message barrier
+__device__ __forceinline__ void pn_mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void pn_mbar_expect(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool pn_mbar_wait(unsigned long long* bar, uint32_t parity) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (long long it = 0; it < PANEL_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void pn_st_async_v4(uint32_t addr, float a, float b, float c, float d, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+                 "f"(a), "f"(b), "f"(c), "f"(d), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void pn_st_async_v2(uint32_t addr, uint32_t a, uint32_t b, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "r"(a), "r"(b), "r"(bar)
+                 : "memory");
+}
+
 constexpr int PANEL_THREADS = 512;
 constexpr int PANEL_MAXC = 16;
 
 template <int WC>
 struct PanelShared {
-    float cand_val[2][PANEL_MAXC];
-    int cand_row[2][PANEL_MAXC];
-    float cand_rowv[2][PANEL_MAXC][WC];
-    float rowj[2][WC];
+    unsigned long long bar[2];                       // message barriers of the two slot buffers
+    __align__(16) float cand_rowv[2][PANEL_MAXC][WC];  // [buf][sender]: candidate row values
+    __align__(16) float rowj[2][WC];                 // [buf]: row j before the interchange
+    __align__(16) uint2 cand_vr[2][PANEL_MAXC];      // [buf][sender]: (|value| bits, row)
     float wbest_val[2][PANEL_THREADS / 32];
     int wbest_row[2][PANEL_THREADS / 32];
     int piv[WC];                      // panel-relative pivot row of each column
     float top[WC][WC + 1];            // final rows 0..wcols-1 of the panel (L11 below the diagonal)
+    float l11[WC][WC + 1];            // L11 rounded to u_f (strictly lower part), for the U12 solve
     int ext_row[32];                  // distinct pivot rows below the panel's diagonal block
     int mv_dst[64], mv_src[64];       // net row moves of the panel's interchanges
     int mv_count;
@@ -147,13 +200,46 @@ __device__ __forceinline__ void argmax_merge(float& v, int& r, float ov, int oro
     if (ov > v || (ov == v && orow < r)) { v = ov; r = orow; }
 }
 
+// Warp-wide argmax of (value, row): the largest value, the lowest row among equal values.
+// Values are magnitudes (>= 0), so their bit patterns order like the values; an invalid
+// candidate (value < 0) enters as (0, 0x7fffffff) and loses against every valid one.
+__device__ __forceinline__ void warp_argmax(float& v, int& row) {
+    const bool ok = v >= 0.0f;
+    const unsigned vb = ok ? __float_as_uint(v) : 0u;
+    const unsigned rb = ok ? (unsigned)row : 0x7fffffffu;
+    const unsigned mv = __reduce_max_sync(0xffffffffu, vb);
+    const unsigned mr = __reduce_min_sync(0xffffffffu, vb == mv ? rb : 0xffffffffu);
+    v = __uint_as_float(mv);
+    row = (int)mr;
+}
+
+// x / p rounded to nearest, with rp = RN(1/p): Markstein's correction step (q0 = RN(x rp),
+// e = x - q0 p exact by FMA, q = RN(q0 + e rp)) gives the correctly rounded quotient when both
+// operands are normal and well inside the exponent range; elsewhere the library division.
+__device__ __forceinline__ bool div_safe(float v) {
+    const uint32_t e = (__float_as_uint(v) >> 23) & 0xffu;
+    return e >= 127u - 96u && e <= 127u + 96u;
+}
+__device__ __forceinline__ float div_rn(float x, float p, float rp, bool p_safe) {
+    if (x == 0.0f) return __int_as_float((__float_as_int(x) ^ __float_as_int(p)) & (int)0x80000000);
+    if (p_safe && div_safe(x)) {
+        const float q0 = x * rp;
+        const float e = fmaf(-q0, p, x);
+        return fmaf(e, rp, q0);
+    }
+    return __fdiv_rn(x, p);
+}
+
 // GEPP of one FP32 panel (rows r0..n-1, wcols <= WC columns) by a cluster of C CTAs, each holding
 // rpc consecutive rows in shared memory. Per column: thread-owned rows give local candidates
-// (computed while the previous column's update ran), one CTA barrier merges them, every CTA
-// pushes its candidate (value, row, row values) and, if it owns row j, row j into every CTA's
-// slot through DSMEM, and one cluster barrier publishes them. Every warp then picks the global
+// (computed while the previous column's update ran) and one CTA barrier merges them. Every CTA
+// then sends its candidate (value, row, row values) and, if it owns row j, row j to every CTA's
+// slot with st.async, which counts the bytes on the receiver's mbarrier; each CTA waits only
+// for its own barrier (no cluster-wide barrier per column). Every warp then picks the global
 // pivot (largest |value|, lowest row on ties) and updates its rows with correctly rounded FP32
 // quotients and fused updates: the FP32 Schur complement of the block-FMA model (Section 3).
+// Slots are double-buffered by column parity: a CTA sends column j + 1 only after it has read
+// everything of column j - 1's slot, so no sender can overwrite a slot still being read.
 template <int WC>
 __global__ void __launch_bounds__(PANEL_THREADS, 1)
 k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, int rpc, int* __restrict__ ipiv,
@@ -186,60 +272,71 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
         if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
         argmax_merge(bv, bi, v, g0 + lr);
     }
-    cluster_barrier();   // every CTA of the cluster is running before the first remote store
+    if (tid == 0) {
+        pn_mbar_init(&sh.bar[0], 1);
+        pn_mbar_init(&sh.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    cluster_barrier();   // every CTA's barriers exist before the first remote message
+    const uint32_t col_bytes = (uint32_t)(C * (8 + 4 * WC) + 4 * WC);
+    bool dead = false;   // a message wait timed out: skip later waits, flag, finish the launch
 
     for (int j = 0; j < wcols; ++j) {
         const int buf = j & 1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            argmax_merge(bv, bi, ov, oi);
-        }
+        if (tid == 0) pn_mbar_expect(&sh.bar[buf], col_bytes);
+        warp_argmax(bv, bi);
         if (lane == 0) { sh.wbest_val[buf][warp] = bv; sh.wbest_row[buf][warp] = bi; }
         __syncthreads();
         // this CTA's candidate, merged redundantly by every warp
         float cv = (lane < NW) ? sh.wbest_val[buf][lane] : -1.0f;
         int cr = (lane < NW) ? sh.wbest_row[buf][lane] : NONE;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, cv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, cr, o);
-            argmax_merge(cv, cr, ov, oi);
-        }
+        warp_argmax(cv, cr);
         {
-            const int q = tid / WC, c = tid - (tid / WC) * WC;   // destination CTA, column
-            if (q < C) {
-                if (c == 0) {
-                    st_cluster_f32(map_shared(&sh.cand_val[buf][rank], q), cv);
-                    st_cluster_s32(map_shared(&sh.cand_row[buf][rank], q), cr);
+            // lane l of warp q sends to CTA q: l < WC/4 a 16-byte chunk of the candidate row,
+            // l == WC/4 the (value, row) pair, the next WC/4 lanes row j (its owner only)
+            constexpr int NCH = WC / 4;
+            const int q = warp, l = lane;
+            if (q < C && l <= 2 * NCH) {
+                const uint32_t rbar = map_shared(&sh.bar[buf], q);
+                if (l < NCH) {
+                    const float* src = (cr != NONE) ? tile + (cr - g0) * TS + 4 * l : nullptr;
+                    pn_st_async_v4(map_shared(&sh.cand_rowv[buf][rank][4 * l], q), src ? src[0] : 0.0f,
+                                   src ? src[1] : 0.0f, src ? src[2] : 0.0f, src ? src[3] : 0.0f, rbar);
+                } else if (l == NCH) {
+                    pn_st_async_v2(map_shared(&sh.cand_vr[buf][rank], q), __float_as_uint(cv), (uint32_t)cr, rbar);
+                } else if (j >= g0 && j < g0 + myrows) {
+                    const int k = l - NCH - 1;
+                    const float* src = tile + (j - g0) * TS + 4 * k;
+                    pn_st_async_v4(map_shared(&sh.rowj[buf][4 * k], q), src[0], src[1], src[2], src[3], rbar);
                 }
-                const float val = (cr != NONE) ? tile[(cr - g0) * TS + c] : 0.0f;
-                st_cluster_f32(map_shared(&sh.cand_rowv[buf][rank][c], q), val);
-                if (j >= g0 && j < g0 + myrows)
-                    st_cluster_f32(map_shared(&sh.rowj[buf][c], q), tile[(j - g0) * TS + c]);
             }
         }
-        cluster_barrier();
-        // global pivot, merged redundantly by every warp
-        float pv = (lane < C) ? sh.cand_val[buf][lane] : -1.0f;
-        int pr = (lane < C) ? sh.cand_row[buf][lane] : NONE;
-        int pq = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, pv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, pr, o);
-            int oq = __shfl_xor_sync(0xffffffffu, pq, o);
-            if (ov > pv || (ov == pv && oi < pr)) { pv = ov; pr = oi; pq = oq; }
+        if (!dead && !pn_mbar_wait(&sh.bar[buf], (uint32_t)((j >> 1) & 1))) {
+            dead = true;
+            local_flag |= DEV_TIMEOUT;
         }
-        if (pr == NONE) {
-            // no finite candidate in the column (all NaN): keep the row order, flag, divide by nothing
+        // global pivot, merged redundantly by every warp
+        float pv = -1.0f;
+        int pr = NONE;
+        if (lane < C) {
+            const uint2 vr = sh.cand_vr[buf][lane];
+            pv = __uint_as_float(vr.x);
+            pr = (int)vr.y;
+        }
+        const unsigned own = (lane < C) ? __float_as_uint(pv) : 0xffffffffu;
+        const int own_row = pr;
+        warp_argmax(pv, pr);
+        int pq = __ffs(__ballot_sync(0xffffffffu, own == __float_as_uint(pv) && own_row == pr)) - 1;
+        if (pr == NONE || pr < j || (int64_t)pr >= h) {
+            // no finite candidate in the column (all NaN), or (after a timed-out wait) no valid
+            // message: keep the row order, flag, divide by nothing
+            local_flag |= (pr == NONE) ? DEV_NONFINITE : DEV_TIMEOUT;
             pr = j;
             pv = 0.0f;
             pq = 0;
-            local_flag |= DEV_NONFINITE;
         }
-        if (pq >= C) pq = 0;
+        if (pq < 0 || pq >= C) pq = 0;
         const float* prow = sh.cand_rowv[buf][pq];
         const float* rj = sh.rowj[buf];
         const float piv = prow[j];
@@ -251,8 +348,16 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
         }
         float pc[WC];
 #pragma unroll
-        for (int c = 0; c < WC; ++c) pc[c] = prow[c];
+        for (int k = 0; k < WC / 4; ++k) {
+            const float4 v = reinterpret_cast<const float4*>(prow)[k];
+            pc[4 * k] = v.x;
+            pc[4 * k + 1] = v.y;
+            pc[4 * k + 2] = v.z;
+            pc[4 * k + 3] = v.w;
+        }
         const bool next = j + 1 < wcols;
+        const float rp = (piv != 0.0f) ? __frcp_rn(piv) : 0.0f;
+        const bool p_safe = div_safe(piv);
         bv = -1.0f;
         bi = NONE;
         for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
@@ -266,26 +371,32 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
                 for (int c = 0; c < WC; ++c) row[c] = rj[c];
             }
             if (g > j) {
-                const float l = (piv != 0.0f) ? __fdiv_rn(row[j], piv) : 0.0f;
+                const float l = (piv != 0.0f) ? div_rn(row[j], piv, rp, p_safe) : 0.0f;
                 row[j] = l;
+                float nv = 0.0f;   // the updated entry of column j + 1
 #pragma unroll
                 for (int cb = 0; cb < WC; cb += 8) {
                     if (cb + 7 > j) {
 #pragma unroll
-                        for (int c = cb; c < cb + 8; ++c)
-                            if (c > j) row[c] = fmaf(-l, pc[c], row[c]);
+                        for (int c = cb; c < cb + 8; ++c) {
+                            if (c > j) {
+                                const float t = fmaf(-l, pc[c], row[c]);
+                                row[c] = t;
+                                if (c == j + 1) nv = t;
+                            }
+                        }
                     }
                 }
                 if (next) {
-                    float v = fabsf(row[j + 1]);
+                    float v = fabsf(nv);
                     if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
                     argmax_merge(bv, bi, v, g);
                 }
             }
         }
     }
-    // no remote access after the last cluster barrier: every CTA finishes on its own
-    __syncthreads();
+    // no CTA leaves while messages to it could still be in flight (only possible after a timeout)
+    cluster_barrier();
     for (int e = tid; e < myrows * WC; e += PANEL_THREADS) {
         int lr = e / WC, c = e - lr * WC;
         if (c < wcols) {
@@ -345,10 +456,10 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     // every source of a chunk is read before any destination is written
     const int nchw = (int)((gmax<int64_t>(ncw, 0) + 31) / 32);
     const int nchl = (int)((gmax<int64_t>(ncl, 0) + 63) / 64);
-    for (int ch = rank; ch < nchw + nchl; ch += C) {
-        if (ch < nchw) {
-            const int64_t cbase = tail.wcol0 + (int64_t)ch * 32;
-            if (cnt > 0) {
+    if (cnt > 0) {
+        for (int ch = rank; ch < nchw + nchl; ch += C) {
+            if (ch < nchw) {
+                const int64_t cbase = tail.wcol0 + (int64_t)ch * 32;
                 float v[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -363,47 +474,57 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
                     const int64_t col = cbase + (e & 31);
                     if (m < cnt && col < tail.wcol1) W[(r0 + sh.mv_dst[m]) * ldw + col] = v[k];
                 }
+            } else {
+                const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw) * 64;
+                uint16_t v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 6;
+                    const int64_t col = cbase + (e & 63);
+                    if (m < cnt && col < tail.lcol1) v[k] = tail.LU[(r0 + sh.mv_src[m]) * tail.ldl + col];
+                }
                 __syncthreads();
-            }
-            if (trsm && tid < 32 && cbase + tid < tail.wcol1) {
-                // forward substitution with the u_f multipliers, one thread per column
-                const int64_t col = cbase + tid;
-                float x[WC];
 #pragma unroll
-                for (int i = 0; i < WC; ++i) x[i] = (i < wcols) ? W[(r0 + i) * ldw + col] : 0.0f;
-#pragma unroll
-                for (int i = 1; i < WC; ++i) {
-                    float acc = x[i];
-#pragma unroll
-                    for (int q = 0; q < WC; ++q)
-                        if (q < i) acc = fmaf(-uf_to_float(float_to_uf(sh.top[i][q], tail.fmt), tail.fmt), x[q], acc);
-                    x[i] = acc;
+                for (int k = 0; k < 8; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 6;
+                    const int64_t col = cbase + (e & 63);
+                    if (m < cnt && col < tail.lcol1) tail.LU[(r0 + sh.mv_dst[m]) * tail.ldl + col] = v[k];
                 }
-#pragma unroll
-                for (int i = 0; i < WC; ++i) {
-                    if (i < wcols) {
-                        const uint16_t u = float_to_uf(x[i], tail.fmt);
-                        tail.LU[(r0 + i) * tail.ldl + col] = u;
-                        W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
-                        tail.UT[col * tail.ldut + i] = u;
-                    }
-                }
-            }
-        } else if (cnt > 0) {
-            const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw) * 64;
-            uint16_t v[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int e = tid + k * PANEL_THREADS, m = e >> 6;
-                const int64_t col = cbase + (e & 63);
-                if (m < cnt && col < tail.lcol1) v[k] = tail.LU[(r0 + sh.mv_src[m]) * tail.ldl + col];
             }
             __syncthreads();
+        }
+    }
+    if (trsm && rank < nchw) {
+        // U12 rows of this CTA's W chunks, one thread per column: forward substitution with the
+        // u_f multipliers, then rounding to u_f (stored in LU, W and UT)
+        for (int e = tid; e < WC * WC; e += PANEL_THREADS) {
+            const int i = e / WC, q = e - (e / WC) * WC;
+            sh.l11[i][q] = (q < i) ? uf_to_float(float_to_uf(sh.top[i][q], tail.fmt), tail.fmt) : 0.0f;
+        }
+        __syncthreads();
+        const int myw = (nchw - rank + C - 1) / C;
+        for (int t = tid; t < myw * 32; t += PANEL_THREADS) {
+            const int64_t col = tail.wcol0 + (int64_t)(rank + (t >> 5) * C) * 32 + (t & 31);
+            if (col >= tail.wcol1) continue;
+            float x[WC];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int e = tid + k * PANEL_THREADS, m = e >> 6;
-                const int64_t col = cbase + (e & 63);
-                if (m < cnt && col < tail.lcol1) tail.LU[(r0 + sh.mv_dst[m]) * tail.ldl + col] = v[k];
+            for (int i = 0; i < WC; ++i) x[i] = (i < wcols) ? W[(r0 + i) * ldw + col] : 0.0f;
+#pragma unroll
+            for (int i = 1; i < WC; ++i) {
+                float acc = x[i];
+#pragma unroll
+                for (int q = 0; q < WC; ++q)
+                    if (q < i) acc = fmaf(-sh.l11[i][q], x[q], acc);
+                x[i] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < WC; ++i) {
+                if (i < wcols) {
+                    const uint16_t u = float_to_uf(x[i], tail.fmt);
+                    tail.LU[(r0 + i) * tail.ldl + col] = u;
+                    W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
+                    tail.UT[col * tail.ldut + i] = u;
+                }
             }
         }
     }
@@ -420,7 +541,8 @@ constexpr int PERM_MAXN = 50000;        // rows addressable by the shared slot t
 constexpr int PERM_MAXK = 256;          // interchanges per plan (outer block width)
 
 __global__ void __launch_bounds__(256) k_swap_plan(const int* __restrict__ ipiv, int64_t k0, int64_t k1,
-                                                   int* __restrict__ plan, int* __restrict__ count) {
+                                                   int* __restrict__ plan, int* __restrict__ count,
+                                                   int* __restrict__ perm) {
     extern __shared__ int slot_of[];            // indexed by row - k1 for rows >= k1
     __shared__ int content[2 * PERM_MAXK];
     __shared__ int rowof[2 * PERM_MAXK];
@@ -505,6 +627,20 @@ __global__ void __launch_bounds__(256) k_swap_plan(const int* __restrict__ ipiv,
         }
     }
     if (tid == 0) *count = c;
+    // the same moves applied to the row permutation (perm[i] = original row now at position i)
+    if (perm) {
+        __shared__ int tmp_s[2 * PERM_MAXK];
+        for (int sidx = tid; sidx < ns; sidx += 256)
+            if (content[sidx] != rowof[sidx]) tmp_s[sidx] = perm[content[sidx]];
+        __syncthreads();
+        for (int sidx = tid; sidx < ns; sidx += 256)
+            if (content[sidx] != rowof[sidx]) perm[rowof[sidx]] = tmp_s[sidx];
+    }
+}
+
+__global__ void k_iota(int* __restrict__ v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (int)i;
 }
 
 constexpr int PERM_THREADS = 1024;
@@ -762,10 +898,11 @@ struct SwapScratch {
     int* count = nullptr;
 };
 
-static gir_status make_plan(const int* ipiv, int64_t k0, int64_t k1, int64_t n, const SwapScratch& sw, cudaStream_t s) {
+static gir_status make_plan(const int* ipiv, int64_t k0, int64_t k1, int64_t n, const SwapScratch& sw, int* perm,
+                            cudaStream_t s) {
     if (k1 - k0 > PERM_MAXK || n - k1 > PERM_MAXN) return GIR_UNSUPPORTED;
     size_t smem = (size_t)gmax<int64_t>(1, n - k1) * sizeof(int);
-    count_launch(), k_swap_plan<<<1, 256, smem, s>>>(ipiv, k0, k1, sw.plan, sw.count);
+    count_launch(), k_swap_plan<<<1, 256, smem, s>>>(ipiv, k0, k1, sw.plan, sw.count, perm);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
@@ -884,7 +1021,7 @@ gir_status lu_scale_quantize(const double* A, int64_t n, int64_t lda, int uf, do
         Rp = R;
         Sp = S;
     }
-    int g = (int)gmin<int64_t>((n * n + 255) / 256, 152 * 32);
+    int g = (int)gmin<int64_t>(n, 152 * 16);
     count_launch(), k_quantize<<<g, 256, 0, s>>>(A, n, lda, Rp, Sp, *mu, W, ldw, flags);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
@@ -894,7 +1031,7 @@ gir_status lu_scale_quantize(const double* A, int64_t n, int64_t lda, int uf, do
 // on the main stream, and (b) all later columns, on a side stream, so (b) runs while the next
 // block's panels (a few SMs) are factored. Events keep every W update, row interchange and
 // UT access ordered: (b)_k finishes before block k+1's end-of-block interchanges and (a)_{k+1}.
-gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv, int64_t n, int fmt,
+gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv, int* perm, int64_t n, int fmt,
                      const LUPlan& plan, uint16_t* UT, int* flags, cudaStream_t s_user) {
     const int w = plan.w;
     const int NB = plan.nb;
@@ -930,6 +1067,7 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
     GIR_CUDA_TRY(cudaStreamWaitEvent(s, ss_.ev_io, 0));
     GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.plan), 4 * PERM_MAXK * sizeof(int), s));
     GIR_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sw.count), sizeof(int), s));
+    if (perm) count_launch(), k_iota<<<(unsigned)gmin<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(perm, n);
     bool b_pending = false;  // a (b) part is running on s2
     gir_status st = GIR_OK;
     // wide column slabs for the bulk (two CTAs per SM), narrow ones for the next block's 256
@@ -950,6 +1088,8 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
         for (int64_t c0 = C0; c0 < Cend; c0 += w) {
             const int wc = (int)gmin<int64_t>(w, Cend - c0);
             int t_ = trace_begin(s);
+            // GIR_TRACE_DETAIL=1: the panel phase also reported per panel-height class
+            const int td_ = trace_detail() ? trace_begin(s) : -1;
             {
                 // the panel kernel also stores the u_f panel, applies its interchanges to the
                 // block's later columns of W and earlier columns of LU, and solves for U12
@@ -957,6 +1097,11 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 GIR_TRY(launch_panel(W, ldw, c0, n, wc, ipiv, flags, plan, tail, s));
             }
             trace_end(t_, "lu panel", s);
+            if (td_ >= 0) {
+                const int64_t h_ = n - c0;
+                trace_end(td_, h_ > 8192 ? "panel h>8192" : h_ > 2048 ? "panel 2048<h<=8192" :
+                               h_ > 512 ? "panel 512<h<=2048" : "panel h<=512", s);
+            }
             GIR_TRY(debug_check("panel", C0, c0, flags, s));
             if (c0 + wc < Cend) {
                 int64_t ncols = Cend - (c0 + wc);
@@ -975,7 +1120,7 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             b_pending = false;
         }
         int t_ = trace_begin(s);
-        GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, s));
+        GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, perm, s));
         GIR_TRY(permute_rows<float>(W, ldw, Cend, n, sw, s));
         GIR_TRY(permute_rows<uint16_t>(LU, ldl, 0, C0, sw, s));
         trace_end(t_, "lu outer swaps", s);

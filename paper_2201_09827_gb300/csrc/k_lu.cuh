@@ -17,7 +17,8 @@ gir_status lu_prepare(LUPlan& plan);
 gir_status lu_scale_quantize(const double* A, int64_t n, int64_t lda, int uf, double* R, double* S, double* mu,
                              float* W, int64_t ldw, unsigned long long* colmax, int* flags, cudaStream_t s);
 // UT: scratch of n x plan.nb 16-bit elements (U12 transposed, K-major operand of the tensor-core update).
-gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv, int64_t n, int fmt,
+// perm (may be null): receives the row permutation, perm[i] = original row now at position i.
+gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv, int* perm, int64_t n, int fmt,
                      const LUPlan& plan, uint16_t* UT, int* flags, cudaStream_t s);
 
 // Test hooks: one panel factorization of an m x w FP32 block (rows 0..m) with a forced

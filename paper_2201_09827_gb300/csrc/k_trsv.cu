@@ -276,23 +276,8 @@ __global__ void k_minv_post_t(const float2* __restrict__ y, const int* __restric
     }
 }
 
-__global__ void k_ipiv_to_perm(const int* __restrict__ ipiv, int64_t n, int* __restrict__ perm) {
-    // single thread: sequential interchanges applied to the identity
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
-    for (int64_t k = 0; k < n; ++k) {
-        int p = ipiv[k];
-        if (p != k) {
-            int a = perm[k];
-            perm[k] = perm[p];
-            perm[p] = a;
-        }
-    }
-}
-
 // ------------------------------------------------------------------ host side
-gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, const int* ipiv,
-                      cudaStream_t s) {
+gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, cudaStream_t s) {
     st.n = n;
     st.nblk = (int)((n + TB - 1) / TB);
     st.fmt = fmt;
@@ -302,7 +287,6 @@ gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n,
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     count_launch(), k_diag_inv<<<st.nblk, TB, smem, s>>>(LU, ldl, n, fmt, 0, st.DL);
     count_launch(), k_diag_inv<<<st.nblk, TB, smem, s>>>(LU, ldl, n, fmt, 1, st.DU);
-    count_launch(), k_ipiv_to_perm<<<1, 32, 0, s>>>(ipiv, n, st.perm);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }

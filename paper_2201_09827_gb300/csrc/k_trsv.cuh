@@ -27,8 +27,7 @@ struct TrsvState {
     int calls = 0;
 };
 
-gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, const int* ipiv,
-                      cudaStream_t s);
+gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, cudaStream_t s);
 // out = fl_u(M^-1 w) (trans = 0) or fl_u(M^-T w) (trans = 1); out may alias w.
 gir_status apply_minv(TrsvState& st, const double* w, double* out, const double* R, const double* S, double mu,
                       int trans, int round32, int* flags, cudaStream_t s);

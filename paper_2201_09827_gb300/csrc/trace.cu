@@ -3,6 +3,7 @@
 // Timing records a pair of CUDA events on the launching stream around each phase without
 // synchronising; elapsed times are resolved and summed per phase name when the report is
 // requested (or when the event pool fills up).
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -33,6 +34,7 @@ struct TraceState {
     std::vector<Slot> slots;
     std::vector<Agg> agg;
     size_t used = 0;
+    int open = 0;   // phases begun and not yet ended (slots may not be recycled meanwhile)
     void resolve() {
         if (slots.empty()) return;
         cudaDeviceSynchronize();
@@ -58,7 +60,7 @@ struct TraceState {
     }
     cudaEvent_t next() {
         if (used >= pool.size()) {
-            if (pool.size() >= 16384) resolve();
+            if (pool.size() >= 16384 && open == 0) resolve();
             if (used >= pool.size()) {
                 cudaEvent_t e;
                 cudaEventCreate(&e);
@@ -78,6 +80,7 @@ int trace_begin(cudaStream_t s) {
     cudaEvent_t a = g_trace.next();
     cudaEventRecord(a, s);
     g_trace.slots.push_back({nullptr, a, nullptr});
+    ++g_trace.open;
     return (int)g_trace.slots.size() - 1;
 }
 
@@ -87,6 +90,16 @@ void trace_end(int slot, const char* name, cudaStream_t s) {
     cudaEventRecord(b, s);
     g_trace.slots[slot].name = name;
     g_trace.slots[slot].b = b;
+    if (g_trace.open > 0) --g_trace.open;
+}
+
+bool trace_detail() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("GIR_TRACE_DETAIL");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return g_trace.on && v == 1;
 }
 
 }  // namespace gir
@@ -94,6 +107,7 @@ void trace_end(int slot, const char* name, cudaStream_t s) {
 extern "C" {
 
 void gir_trace_enable(int on) {
+    gir::g_trace.open = 0;
     gir::g_trace.resolve();
     gir::g_trace.agg.clear();
     gir::g_trace.on = on != 0;

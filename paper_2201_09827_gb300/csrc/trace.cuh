@@ -6,4 +6,6 @@ namespace gir {
 bool trace_on();
 int trace_begin(cudaStream_t s);
 void trace_end(int slot, const char* name, cudaStream_t s);
+// GIR_TRACE_DETAIL=1 (with tracing on): extra per-class phases for diagnosis
+bool trace_detail();
 }  // namespace gir
