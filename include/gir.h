@@ -66,9 +66,14 @@ typedef struct {
     int carry_mode;     /* 0: recompute QR(A~ Y~) at each new refinement step (Algorithm 3, lines 1-4);
                            1: reuse (U_k, C_k), which satisfy A~ U_k = C_k already */
     int max_its;        /* cap on Arnoldi steps per GCRO-DR call (<= 0: 20*m) */
-    int lu_nb;          /* LU outer block width (<= 0: default) */
-    unsigned flags;     /* reserved, must be 0 */
+    int lu_nb;          /* LU outer block width (<= 0: the tuned value for this size class, if
+                           gir_autotune has measured one, else 256) */
+    unsigned flags;     /* GIR_FLAG_* bits; other bits must be 0 */
 } gir_params;
+
+/* gir_batch_solve: measure (gir_autotune) the size classes of the batch that have no tuned
+ * values yet before solving. */
+#define GIR_FLAG_AUTOTUNE 0x1u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64
@@ -113,11 +118,28 @@ gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const 
                              double* lambda, gir_info* info, void* stream);
 
 /* Batch of independent systems A_i x_i = b_i of different sizes n[i] (host array), each
- * with its own factorization and recycle space. A, b, x: host arrays of device pointers.
- * infos: host array of nsys entries (may be NULL). Returns the worst status. Not in the paper. */
+ * solved by Algorithm 4 with its own factorization and recycle space. A, b, x: host arrays of
+ * device pointers (lda: host array). infos: host array of nsys entries (may be NULL).
+ * The systems run concurrently, largest n first, on a pool of worker streams (one host thread
+ * each); the pool size and each system's LU block width come from the autotuner's table
+ * (gir_autotune; GIR_FLAG_AUTOTUNE tunes missing size classes first) or from defaults.
+ * The workers start after the work already enqueued on `stream`, and `stream` waits for all
+ * of them. Returns GIR_OK, else the worst status of a system. Not in the paper. */
 gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
                            const double* const* b, double* const* x, const gir_params* params,
                            gir_info* infos, void* stream);
+
+/* Autotuner (not in the paper). For each size class (n in (2^(c-1), 2^c]) of the count sizes in
+ * n (host array), times gir_factor on a synthetic matrix of the class's largest order with LU
+ * outer block widths 64, 128 and 256, and times a synthetic batch of factorizations of the
+ * median size with 2, 4, 8 and 16 concurrent workers; the fastest choices go into a process-wide
+ * table used by gir_factor (when params->lu_nb <= 0) and gir_batch_solve. Allocates temporary
+ * device memory; synchronises. Classes already in the table are not measured again. */
+gir_status gir_autotune(const int64_t* n, int count, void* stream);
+
+/* Writes the tuned table as text lines ("class c: n <= N, lu_nb B, ms T" and "workers K") into
+ * buf (host, buflen bytes, NUL-terminated) and returns the full length needed. */
+int gir_tune_report(char* buf, int buflen);
 
 void gir_free(gir_handle* h);
 const char* gir_status_string(gir_status s);

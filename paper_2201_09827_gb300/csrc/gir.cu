@@ -4,12 +4,14 @@
 // k_vec.cu (residual, A v, tall-skinny products) and k_small.cu (Givens, least squares,
 // harmonic Ritz, QR). The host only sequences launches on the caller's stream and reads
 // back a few scalars per Arnoldi step (convergence flag) and per refinement step (norms).
+#include <atomic>
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
 
+#include "gir_batch.cuh"
 #include "gir_internal.cuh"
 #include "k_lu.cuh"
 #include "k_small.cuh"
@@ -99,10 +101,10 @@ gir_status dalloc_t(T** p, size_t count) {
 // told to keep freed memory (release threshold = max) so that repeated factorizations reuse
 // it without going back to the driver.
 gir_status pool_alloc(void** p, size_t bytes, cudaStream_t s) {
-    static int configured_dev = -1;
+    static std::atomic<int> configured_dev{-1};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (configured_dev != dev) {
+    if (configured_dev.load() != dev) {
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
             uint64_t thr = ~0ull;
@@ -125,21 +127,27 @@ gir_status pool_alloc_t(T** p, size_t count, cudaStream_t s) {
     return pool_alloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
 }
 
-void free_handle(gir_handle* h) {
+// Frees the handle's memory on stream s; the caller guarantees that no kernel that uses it is
+// still queued anywhere else (free_handle synchronises the device for that).
+void free_handle_on(gir_handle* h, cudaStream_t s) {
     if (!h) return;
-    cudaDeviceSynchronize();   // no kernel of any stream may still use the handle's memory
     void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.perm, h->trsv.z, h->trsv.y1,
                     h->trsv.y2, h->trsv.ready, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
                     h->scratch, h->st, h->qh, h->dsc, h->dflags};
-    // pool memory: every use is finished (callers synchronise the device first)
     for (void* q : ptrs)
-        if (q) cudaFreeAsync(q, 0);
+        if (q) cudaFreeAsync(q, s);
     if (h->hsc) cudaFreeHost(h->hsc);
     if (h->hst) cudaFreeHost(h->hst);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;
+}
+
+void free_handle(gir_handle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();   // no kernel of any stream may still use the handle's memory
+    free_handle_on(h, 0);
 }
 
 double unit_roundoff(gir_prec p) {
@@ -157,7 +165,7 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->k < 0 || p->k >= p->m || p->k > GIR_MAX_K) return GIR_INVALID_ARG;
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
-    if (p->flags != 0) return GIR_INVALID_ARG;
+    if ((p->flags & ~GIR_FLAG_AUTOTUNE) != 0) return GIR_INVALID_ARG;
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
     if (p->ur != GIR_FP64 && p->ur != GIR_DD) return GIR_UNSUPPORTED;
@@ -555,6 +563,8 @@ __global__ void k_colabs(const double* __restrict__ A, int64_t n, int64_t lda, d
 
 }  // namespace
 
+void gir::release_handle_on(gir_handle* h, cudaStream_t s) { free_handle_on(h, s); }
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -656,7 +666,10 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     unsigned long long* colmax = nullptr;
     uint16_t* UT = nullptr;
     st = lu_prepare(h->plan);
-    if (params->lu_nb > 0) h->plan.nb = (params->lu_nb + h->plan.w - 1) / h->plan.w * h->plan.w;
+    {
+        const int nb = params->lu_nb > 0 ? params->lu_nb : tuned_lu_nb(n);
+        if (nb > 0) h->plan.nb = (nb + h->plan.w - 1) / h->plan.w * h->plan.w;
+    }
     if (st == GIR_OK) st = pool_alloc_t(&W, (size_t)n * ldw, s);
     if (st == GIR_OK) st = pool_alloc_t(&colmax, (size_t)n, s);
     if (st == GIR_OK) st = pool_alloc_t(&UT, (size_t)n * h->plan.nb + 64, s);
@@ -724,27 +737,6 @@ gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const 
     }
     if (info) info->ms_factor = (float)h->hsc[SC_COUNT - 2];
     return refine(h, A, lda, g, lambda, info, 1, s);
-}
-
-gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
-                           const double* const* b, double* const* x, const gir_params* params, gir_info* infos,
-                           void* stream) {
-    if (nsys < 0 || (nsys > 0 && (!n || !A || !lda || !b || !x || !params))) return GIR_INVALID_ARG;
-    gir_status worst = GIR_OK;
-    for (int i = 0; i < nsys; ++i) {
-        gir_handle* h = nullptr;
-        gir_info loc;
-        memset(&loc, 0, sizeof(loc));
-        gir_status s = gir_factor(A[i], n[i], lda[i], params, stream, &h);
-        if (s == GIR_OK) {
-            s = gir_solve(h, A[i], lda[i], b[i], x[i], &loc, stream);
-            gir_free(h);
-        }
-        loc.status = s;
-        if (infos) infos[i] = loc;
-        if (s != GIR_OK && (worst == GIR_OK || worst == GIR_NOT_CONVERGED)) worst = s;
-    }
-    return worst;
 }
 
 gir_status gir_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b, double* r,

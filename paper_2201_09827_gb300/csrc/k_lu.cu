@@ -857,12 +857,12 @@ __global__ void __launch_bounds__(256) k_gemm_sub_simt(float* __restrict__ Cm, i
 
 // ------------------------------------------------------------------ host driver
 // GIR_DEBUG_LU=1: synchronise after every stage and report the first stage that raises a flag.
+static int debug_lu_env() {
+    const char* e = getenv("GIR_DEBUG_LU");
+    return (e && e[0] == '1') ? 1 : 0;
+}
 static int debug_lu() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("GIR_DEBUG_LU");
-        v = (e && e[0] == '1') ? 1 : 0;
-    }
+    static const int v = debug_lu_env();
     return v;
 }
 static gir_status debug_check(const char* stage, int64_t a, int64_t b, int* flags, cudaStream_t s) {

@@ -3,6 +3,7 @@
 // Timing records a pair of CUDA events on the launching stream around each phase without
 // synchronising; elapsed times are resolved and summed per phase name when the report is
 // requested (or when the event pool fills up).
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -14,9 +15,9 @@
 
 namespace gir {
 
-static unsigned long long g_launches = 0;
-void count_launch() { ++g_launches; }
-unsigned long long launch_count() { return g_launches; }
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
 
 namespace {
 struct Slot {
@@ -71,12 +72,14 @@ struct TraceState {
     }
 };
 TraceState g_trace;
+std::mutex g_trace_mu;   // the batch runs solves on several host threads
 }  // namespace
 
 bool trace_on() { return g_trace.on; }
 
 int trace_begin(cudaStream_t s) {
     if (!g_trace.on) return -1;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
     cudaEvent_t a = g_trace.next();
     cudaEventRecord(a, s);
     g_trace.slots.push_back({nullptr, a, nullptr});
@@ -85,7 +88,9 @@ int trace_begin(cudaStream_t s) {
 }
 
 void trace_end(int slot, const char* name, cudaStream_t s) {
-    if (!g_trace.on || slot < 0 || slot >= (int)g_trace.slots.size()) return;
+    if (!g_trace.on) return;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (slot < 0 || slot >= (int)g_trace.slots.size()) return;
     cudaEvent_t b = g_trace.next();
     cudaEventRecord(b, s);
     g_trace.slots[slot].name = name;
@@ -93,12 +98,13 @@ void trace_end(int slot, const char* name, cudaStream_t s) {
     if (g_trace.open > 0) --g_trace.open;
 }
 
+static int env_flag(const char* name) {
+    const char* e = getenv(name);
+    return (e && e[0] == '1') ? 1 : 0;
+}
+
 bool trace_detail() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("GIR_TRACE_DETAIL");
-        v = (e && e[0] == '1') ? 1 : 0;
-    }
+    static const int v = env_flag("GIR_TRACE_DETAIL");
     return g_trace.on && v == 1;
 }
 
@@ -107,6 +113,7 @@ bool trace_detail() {
 extern "C" {
 
 void gir_trace_enable(int on) {
+    std::lock_guard<std::mutex> lk(gir::g_trace_mu);
     gir::g_trace.open = 0;
     gir::g_trace.resolve();
     gir::g_trace.agg.clear();
@@ -114,6 +121,7 @@ void gir_trace_enable(int on) {
 }
 
 int gir_trace_report(char* buf, int buflen) {
+    std::lock_guard<std::mutex> lk(gir::g_trace_mu);
     gir::g_trace.resolve();
     std::string out;
     char line[256];
@@ -130,6 +138,6 @@ int gir_trace_report(char* buf, int buflen) {
     return (int)out.size();
 }
 
-unsigned long long gir_launch_count(void) { return gir::g_launches; }
+unsigned long long gir_launch_count(void) { return gir::g_launches.load(); }
 
 }  // extern "C"

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import torch
 
@@ -47,6 +47,8 @@ SYMBOLS = {
     "gir_batch_solve": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(CParams), C.POINTER(CInfo),
                                   C.c_void_p]),
+    "gir_autotune": (C.c_int, [C.POINTER(C.c_int64), C.c_int, C.c_void_p]),
+    "gir_tune_report": (C.c_int, [C.c_char_p, C.c_int]),
     "gir_free": (None, [C.c_void_p]),
     "gir_status_string": (C.c_char_p, [C.c_int]),
     "gir_handle_n": (C.c_int64, [C.c_void_p]),
@@ -120,10 +122,14 @@ class Params:
     carry_mode: int = 1
     max_its: int = 0
     lu_nb: int = 0
+    flags: int = 0
 
     def c(self) -> CParams:
         return CParams(PREC[self.uf], PREC[self.u], PREC[self.ur], PREC[self.ua], self.m, self.k, self.tau, self.imax,
-                       self.target_berr, self.carry_mode, self.max_its, self.lu_nb, 0)
+                       self.target_berr, self.carry_mode, self.max_its, self.lu_nb, self.flags)
+
+
+GIR_FLAG_AUTOTUNE = 0x1
 
 
 @dataclass
@@ -388,7 +394,28 @@ def solve(A, b, params: Params | None = None, stream=None):
     return x, info
 
 
-def batch_solve(As, bs, params: Params, stream=None):
+def autotune(sizes, stream=None):
+    """Measure LU block widths for the size classes of `sizes` and the batch worker count."""
+    sizes = [int(v) for v in sizes]
+    arr = (C.c_int64 * len(sizes))(*sizes)
+    st = load().gir_autotune(arr, len(sizes), _stream(stream))
+    if st != GIR_OK:
+        raise GirError(st, "gir_autotune")
+
+
+def tune_report() -> str:
+    lib = load()
+    need = lib.gir_tune_report(None, 0)
+    buf = C.create_string_buffer(need)
+    lib.gir_tune_report(buf, need)
+    return buf.value.decode()
+
+
+def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False):
+    """Solve independent systems A_i x_i = b_i concurrently (longest first over worker streams).
+    autotune=True measures missing size classes first (GIR_FLAG_AUTOTUNE)."""
+    if autotune:
+        params = replace(params, flags=params.flags | GIR_FLAG_AUTOTUNE)
     lib = load()
     nsys = len(As)
     ns = (C.c_int64 * nsys)(*[A.shape[0] for A in As])

@@ -293,3 +293,45 @@ def test_status_paths(pkg):
     x, info = F.solve(cuda(A), cuda(bn))
     assert info.status == gir.GIR_NONFINITE
     F.close()
+
+
+def test_batch_parity_with_oracle(pkg):
+    """Twelve independent systems of uneven order and conditioning solved concurrently by
+    gir_batch_solve: each one matches its own oracle solve (status, backward error within 4x,
+    iteration count within 10%)."""
+    rng = np.random.default_rng(3)
+    sizes = [int(v) for v in rng.integers(96, 700, 12)]
+    kappas = 10.0 ** rng.uniform(2, 4, 12)
+    As = [randsvd(n, kp, seed=10 + i) for i, (n, kp) in enumerate(zip(sizes, kappas))]
+    bs = [A @ normal_vector(A.shape[0], 100 + i) for i, A in enumerate(As)]
+    m, k, tau = 30, 8, 1e-8
+    prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=m, k=k, tau=tau, imax=10, target_berr=-1.0)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    assert st in (0, 1)
+    op = OP(uf="bf16", u="fp64", ur="fp64", ua="u", m=m, k=k, tau=tau, imax=10, target=None, lu_w=32,
+            max_its=20 * m, carry_mode=1)
+    for A, b, x, info in zip(As, bs, xs, infos):
+        xo, io, _, _ = osolve(A, b, op)
+        assert_parity(A, b, x.cpu().numpy(), info, xo, io, "fp64")
+
+
+def test_autotune_and_tuned_batch(pkg):
+    """The autotuner fills one entry per size class with a block width it measured and a worker
+    count; a batch with GIR_FLAG_AUTOTUNE measures its new class first and still solves to 2u."""
+    pkg.autotune([200, 300, 600])
+    rep = pkg.tune_report()
+    classes = {int(l.split()[1].rstrip(":")): int(l.split("lu_nb")[1].split(",")[0]) for l in rep.splitlines()
+               if l.startswith("class")}
+    assert {8, 9, 10} <= set(classes)
+    assert set(classes.values()) <= {64, 128, 256}
+    workers = int([l for l in rep.splitlines() if l.startswith("workers")][0].split()[1])
+    assert workers in (2, 4, 8, 16)
+    sizes = [1500, 1100, 96]
+    As = [randsvd(n, 1e3, seed=n) for n in sizes]
+    bs = [rhs_uniform(n, n + 1) for n in sizes]
+    prm = pkg.Params(uf="bf16", m=30, k=8, tau=1e-8, target_berr=-1.0)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, autotune=True)
+    assert st == 0
+    assert "class 11:" in pkg.tune_report()
+    for A, b, x in zip(As, bs, xs):
+        assert normwise_berr(A, x.cpu().numpy(), b) <= 2 * 2.0 ** -53 * 4
