@@ -166,7 +166,7 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
     if ((p->flags & ~GIR_FLAG_AUTOTUNE) != 0) return GIR_INVALID_ARG;
-    if (p->uf != GIR_BF16 && p->uf != GIR_FP16) return GIR_UNSUPPORTED;
+    if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
     if (p->ur != GIR_FP64 && p->ur != GIR_DD) return GIR_UNSUPPORTED;
     if (p->ua != GIR_FP64) return GIR_UNSUPPORTED;
@@ -666,7 +666,10 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     unsigned long long* colmax = nullptr;
     uint16_t* UT = nullptr;
     st = lu_prepare(h->plan);
-    {
+    if (params->uf == GIR_FP8_E4M3) {
+        h->plan.fp8 = 1;     // block columns are the 128-wide scale tiles of the FP8 model
+        h->plan.nb = 128;
+    } else {
         const int nb = params->lu_nb > 0 ? params->lu_nb : tuned_lu_nb(n);
         if (nb > 0) h->plan.nb = (nb + h->plan.w - 1) / h->plan.w * h->plan.w;
     }

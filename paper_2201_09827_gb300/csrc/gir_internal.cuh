@@ -116,10 +116,10 @@ __device__ __forceinline__ ff ff_norm(float h, float l) {
 }
 
 // ----------------------------------------------------------------------------- factor format
-// Factors are stored as 16-bit patterns: bf16 or fp16 (u_f). fp8 factors are stored as
-// e4m3 values widened to fp16 bit patterns of (value / tile scale); the tile scale lives
-// in a separate array.
-enum FactorFmt : int { FF_BF16 = 0, FF_FP16 = 1, FF_E4M3 = 2 };
+// Factors are stored as 16-bit patterns: bf16 or fp16 (u_f). FP8-E4M3 factors (values
+// RN_e4m3(x s) / s with a power-of-two scale s per 128 x 128 tile) have at most 4 significant
+// bits and are stored exactly as bf16 patterns, so they use FF_BF16 from the factorization on.
+enum FactorFmt : int { FF_BF16 = 0, FF_FP16 = 1 };
 
 __device__ __forceinline__ float uf_to_float(uint16_t v, int fmt) {
     if (fmt == FF_BF16) return __bfloat162float(__ushort_as_bfloat16(v));

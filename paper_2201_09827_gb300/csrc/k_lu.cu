@@ -9,6 +9,10 @@
 // inside an outer block, panels of w columns are factored by one thread-block cluster each
 // (the whole panel lives in the cluster's distributed shared memory; one cluster barrier
 // per column carries the pivot search), followed by the in-block TRSM/GEMM updates.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "gir_internal.cuh"
 #include "k_lu.cuh"
 #include "trace.cuh"
@@ -190,10 +194,14 @@ struct PanelTail {
     uint16_t* LU;          // null: no u_f store and no LU interchanges
     int64_t ldl;
     int fmt;
-    int64_t wcol0, wcol1;  // W columns [wcol0, wcol1) receive the interchanges
+    int64_t wcol0, wcol1;  // W columns [wcol0, wcol1) receive the interchanges (and the U12 solve)
     int64_t lcol0, lcol1;  // LU columns [lcol0, lcol1) receive them
-    uint16_t* UT;          // non-null: also U12 = fl_uf(L11^-1 W[panel rows, wcol0:wcol1]) into
-    int64_t ldut;          //   LU, W and UT[col * ldut + i] (FP32 substitution, then rounded)
+    uint16_t* UT;          // U12 transposed (u12_mode 1): UT[col * ldut + i]
+    int64_t ldut;
+    int64_t w2col0, w2col1;  // further W columns receiving the interchanges only
+    int u12_mode;          // 0: none; 1: U12 = fl_uf(L11^-1 W[panel rows, wcol0:wcol1]) by FP32
+                           // substitution with the rounded L11, into LU, W and UT; 2: the same in
+                           // FP32 with the unrounded L11, into W only (FP8 blocks, rounded later)
 };
 
 __device__ __forceinline__ void argmax_merge(float& v, int& r, float ov, int orow) {
@@ -408,8 +416,9 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     if (local_flag) atomicOr(flags, local_flag);
 
     const int64_t ncw = tail.wcol1 - tail.wcol0;
+    const int64_t ncw2 = tail.w2col1 - tail.w2col0;
     const int64_t ncl = tail.LU ? tail.lcol1 - tail.lcol0 : 0;
-    if (ncw <= 0 && ncl <= 0) return;
+    if (ncw <= 0 && ncw2 <= 0 && ncl <= 0) return;
     // net effect of the interchanges ipiv[r0 .. r0+wcols) as row moves (dst <- src): replay them
     // on slot contents held in one warp's registers (slots 0..31 panel rows, 32.. the distinct
     // pivot rows below the diagonal block, numbered by first use)
@@ -450,32 +459,35 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     }
     __syncthreads();
     const int cnt = sh.mv_count;
-    const bool trsm = tail.UT != nullptr;
+    const bool trsm = tail.u12_mode != 0;
     if (cnt == 0 && !trsm) return;
     // column chunks (32 FP32 columns of W, 64 u_f columns of LU) spread over the cluster's CTAs;
     // every source of a chunk is read before any destination is written
     const int nchw = (int)((gmax<int64_t>(ncw, 0) + 31) / 32);
+    const int nchw2 = (int)((gmax<int64_t>(ncw2, 0) + 31) / 32);
     const int nchl = (int)((gmax<int64_t>(ncl, 0) + 63) / 64);
     if (cnt > 0) {
-        for (int ch = rank; ch < nchw + nchl; ch += C) {
-            if (ch < nchw) {
-                const int64_t cbase = tail.wcol0 + (int64_t)ch * 32;
+        for (int ch = rank; ch < nchw + nchw2 + nchl; ch += C) {
+            if (ch < nchw + nchw2) {
+                const bool second = ch >= nchw;
+                const int64_t cbase = second ? tail.w2col0 + (int64_t)(ch - nchw) * 32 : tail.wcol0 + (int64_t)ch * 32;
+                const int64_t cend = second ? tail.w2col1 : tail.wcol1;
                 float v[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int e = tid + k * PANEL_THREADS, m = e >> 5;
                     const int64_t col = cbase + (e & 31);
-                    if (m < cnt && col < tail.wcol1) v[k] = W[(r0 + sh.mv_src[m]) * ldw + col];
+                    if (m < cnt && col < cend) v[k] = W[(r0 + sh.mv_src[m]) * ldw + col];
                 }
                 __syncthreads();
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int e = tid + k * PANEL_THREADS, m = e >> 5;
                     const int64_t col = cbase + (e & 31);
-                    if (m < cnt && col < tail.wcol1) W[(r0 + sh.mv_dst[m]) * ldw + col] = v[k];
+                    if (m < cnt && col < cend) W[(r0 + sh.mv_dst[m]) * ldw + col] = v[k];
                 }
             } else {
-                const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw) * 64;
+                const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw - nchw2) * 64;
                 uint16_t v[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -496,10 +508,13 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     }
     if (trsm && rank < nchw) {
         // U12 rows of this CTA's W chunks, one thread per column: forward substitution with the
-        // u_f multipliers, then rounding to u_f (stored in LU, W and UT)
+        // u_f multipliers, then rounding to u_f (stored in LU, W and UT); in mode 2 the FP32
+        // multipliers and no rounding (W only)
+        const bool rnd = tail.u12_mode == 1;
         for (int e = tid; e < WC * WC; e += PANEL_THREADS) {
             const int i = e / WC, q = e - (e / WC) * WC;
-            sh.l11[i][q] = (q < i) ? uf_to_float(float_to_uf(sh.top[i][q], tail.fmt), tail.fmt) : 0.0f;
+            const float t = sh.top[i][q];
+            sh.l11[i][q] = (q < i) ? (rnd ? uf_to_float(float_to_uf(t, tail.fmt), tail.fmt) : t) : 0.0f;
         }
         __syncthreads();
         const int myw = (nchw - rank + C - 1) / C;
@@ -520,10 +535,14 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
 #pragma unroll
             for (int i = 0; i < WC; ++i) {
                 if (i < wcols) {
-                    const uint16_t u = float_to_uf(x[i], tail.fmt);
-                    tail.LU[(r0 + i) * tail.ldl + col] = u;
-                    W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
-                    tail.UT[col * tail.ldut + i] = u;
+                    if (rnd) {
+                        const uint16_t u = float_to_uf(x[i], tail.fmt);
+                        tail.LU[(r0 + i) * tail.ldl + col] = u;
+                        W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
+                        tail.UT[col * tail.ldut + i] = u;
+                    } else {
+                        W[(r0 + i) * ldw + col] = x[i];
+                    }
                 }
             }
         }
@@ -693,7 +712,7 @@ constexpr size_t trsm_band_smem() {
     return (size_t)TB_MAXNB * (TBC + 1) * sizeof(float) + 2 * (size_t)TB_MAXNB * TB_LS * sizeof(uint16_t);
 }
 
-template <int TBC>
+template <int TBC, bool RND>
 __global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, int64_t ldl, float* __restrict__ W,
                                                    int64_t ldw, int64_t r0, int nb, int64_t col0, int64_t col1,
                                                    int fmt, uint16_t* __restrict__ UT, int64_t ldut) {
@@ -753,13 +772,19 @@ __global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, in
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (i < wb) {
-                    const uint16_t u = float_to_uf(x[i], fmt);
-                    const float uv = uf_to_float(u, fmt);
-                    X[(b0 + i) * XS + c] = uv;
-                    if (c < width) {
-                        W[(r0 + b0 + i) * ldw + c0 + c] = uv;
-                        LU[(r0 + b0 + i) * ldl + c0 + c] = u;
-                        UT[(c0 + c) * ldut + b0 + i] = u;
+                    if (RND) {
+                        const uint16_t u = float_to_uf(x[i], fmt);
+                        const float uv = uf_to_float(u, fmt);
+                        X[(b0 + i) * XS + c] = uv;
+                        if (c < width) {
+                            W[(r0 + b0 + i) * ldw + c0 + c] = uv;
+                            LU[(r0 + b0 + i) * ldl + c0 + c] = u;
+                            UT[(c0 + c) * ldut + b0 + i] = u;
+                        }
+                    } else {
+                        // FP8 blocks: FP32 values throughout, rounded tile by tile afterwards
+                        X[(b0 + i) * XS + c] = x[i];
+                        if (c < width) W[(r0 + b0 + i) * ldw + c0 + c] = x[i];
                     }
                 }
             }
@@ -802,12 +827,86 @@ __global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, in
     }
 }
 
+// ------------------------------------------------------------------ FP8-E4M3 operand tiles
+// Rounding of an operand region to e4m3 with one power-of-two scale per 128 x 128 tile of the
+// global tile grid: s = 2^floor(log2(448 / max|tile|)) (1 for an all-zero tile), value =
+// RN_sat_e4m3(x s) / s. The value has at most 4 significant bits, so it is stored exactly as a
+// bf16 bit pattern in LU (and transposed in UT): the bf16 tensor-core update then multiplies
+// exactly the e4m3 operands the block-scaled FP8 model prescribes, with FP32 accumulation.
+// part: TILE_FULL every entry; TILE_LOWER entries below the diagonal (row > col);
+// TILE_UPPER entries on and above it. One CTA per tile.
+enum { TILE_FULL = 0, TILE_LOWER = 1, TILE_UPPER = 2 };
+constexpr int FP8_TILE = 128;
+
+__global__ void __launch_bounds__(256) k_quant_tiles(const float* __restrict__ W, int64_t ldw, uint16_t* __restrict__ LU,
+                                                     int64_t ldl, uint16_t* __restrict__ UT, int64_t ldut,
+                                                     int64_t ut_row0, int64_t r0, int64_t nrows, int64_t c0,
+                                                     int64_t ncols, int part) {
+    __shared__ float wmax[8];
+    const int tid = threadIdx.x;
+    // tile (tr, tc) of the global grid that intersects the region
+    const int64_t tr0 = (r0 / FP8_TILE + blockIdx.y) * FP8_TILE;
+    const int64_t tc0 = (c0 / FP8_TILE + blockIdx.x) * FP8_TILE;
+    const int64_t rb = gmax<int64_t>(tr0, r0), re = gmin<int64_t>(tr0 + FP8_TILE, r0 + nrows);
+    const int64_t cb = gmax<int64_t>(tc0, c0), ce = gmin<int64_t>(tc0 + FP8_TILE, c0 + ncols);
+    if (rb >= re || cb >= ce) return;
+    const int64_t h = re - rb, w = ce - cb;
+    auto inside = [&](int64_t i, int64_t j) {
+        return part == TILE_FULL || (part == TILE_LOWER ? i > j : i <= j);
+    };
+    float m = 0.0f;
+    for (int64_t e = tid; e < h * w; e += 256) {
+        const int64_t i = rb + e / w, j = cb + e % w;
+        if (inside(i, j)) m = fmaxf(m, fabsf(W[i * ldw + j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    m = wmax[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) m = fmaxf(m, wmax[k]);
+    double sc = 1.0;
+    if (m > 0.0f) {
+        int ex = 0;
+        frexp(448.0 / (double)m, &ex);   // 448 / m = f 2^ex with f in [0.5, 1)
+        sc = ldexp(1.0, ex - 1);
+    }
+    const float s = (float)sc, inv = (float)(1.0 / sc);
+    for (int64_t e = tid; e < h * w; e += 256) {
+        const int64_t i = rb + e / w, j = cb + e % w;
+        if (!inside(i, j)) continue;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(W[i * ldw + j] * s, __NV_SATFINITE, __NV_E4M3);
+        const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        const float v = __half2float(__half(hr)) * inv;
+        const uint16_t b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        LU[i * ldl + j] = b;
+        if (UT) UT[j * ldut + (i - ut_row0)] = b;
+    }
+}
+
+static void quantize_tiles(const float* W, int64_t ldw, uint16_t* LU, int64_t ldl, uint16_t* UT, int64_t ldut,
+                           int64_t r0, int64_t nrows, int64_t c0, int64_t ncols, int part, cudaStream_t s) {
+    if (nrows <= 0 || ncols <= 0) return;
+    const unsigned gx = (unsigned)((c0 + ncols - 1) / FP8_TILE - c0 / FP8_TILE + 1);
+    const unsigned gy = (unsigned)((r0 + nrows - 1) / FP8_TILE - r0 / FP8_TILE + 1);
+    count_launch(), k_quant_tiles<<<dim3(gx, gy), 256, 0, s>>>(W, ldw, LU, ldl, UT, ldut, r0, r0, nrows, c0, ncols, part);
+}
+
 // ------------------------------------------------------------------ SIMT trailing update
 // C[M x N] -= A[M x K] * B[K x N] with u_f operands (16-bit, row-major) and FP32 accumulation.
 // 128 x 128 tile, BK = 16, 256 threads, 8 x 8 outputs per thread.
+template <typename T>
+__device__ __forceinline__ float operand_value(T v, int fmt);
+template <>
+__device__ __forceinline__ float operand_value<uint16_t>(uint16_t v, int fmt) { return uf_to_float(v, fmt); }
+template <>
+__device__ __forceinline__ float operand_value<float>(float v, int) { return v; }
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_sub_simt(float* __restrict__ Cm, int64_t ldc,
-                                                       const uint16_t* __restrict__ Am, int64_t lda,
-                                                       const uint16_t* __restrict__ Bm, int64_t ldb, int M, int N,
+                                                       const T* __restrict__ Am, int64_t lda,
+                                                       const T* __restrict__ Bm, int64_t ldb, int M, int N,
                                                        int K, int fmt) {
     __shared__ float As[16][128 + 4];
     __shared__ float Bs[16][128 + 4];
@@ -825,10 +924,10 @@ __global__ void __launch_bounds__(256) k_gemm_sub_simt(float* __restrict__ Cm, i
             int e = tid + t * 256;           // 0..2047
             int mi = e >> 4, kk = e & 15;    // A: 128 rows x 16 k
             int gm = m0 + mi, gk = k0 + kk;
-            As[kk][mi] = (gm < M && gk < K) ? uf_to_float(Am[(int64_t)gm * lda + gk], fmt) : 0.0f;
+            As[kk][mi] = (gm < M && gk < K) ? operand_value<T>(Am[(int64_t)gm * lda + gk], fmt) : 0.0f;
             int kb = e >> 7, ni = e & 127;   // B: 16 k x 128 cols
             int gkb = k0 + kb, gn = n0 + ni;
-            Bs[kb][ni] = (gkb < K && gn < N) ? uf_to_float(Bm[(int64_t)gkb * ldb + gn], fmt) : 0.0f;
+            Bs[kb][ni] = (gkb < K && gn < N) ? operand_value<T>(Bm[(int64_t)gkb * ldb + gn], fmt) : 0.0f;
         }
         __syncthreads();
 #pragma unroll
@@ -879,6 +978,16 @@ static gir_status debug_check(const char* stage, int64_t a, int64_t b, int* flag
     return GIR_OK;
 }
 
+// C -= A B with FP32 operands (inside an FP8 block column, before its operands are rounded).
+static gir_status gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
+                               int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return GIR_OK;
+    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
+    count_launch(), k_gemm_sub_simt<float><<<grid, 256, 0, s>>>(C, ldc, A, lda, B, ldb, (int)M, (int)N, (int)K, 0);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
 static gir_status gemm_sub(float* C, int64_t ldc, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                            const uint16_t* Bt, int64_t ldbt, int64_t M, int64_t N, int64_t K, int fmt,
                            const LUPlan& plan, int* flags, cudaStream_t s) {
@@ -888,7 +997,7 @@ static gir_status gemm_sub(float* C, int64_t ldc, const uint16_t* A, int64_t lda
         if (st != GIR_UNSUPPORTED) return st;
     }
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
-    count_launch(), k_gemm_sub_simt<<<grid, 256, 0, s>>>(C, ldc, A, lda, B, ldb, (int)M, (int)N, (int)K, fmt);
+    count_launch(), k_gemm_sub_simt<uint16_t><<<grid, 256, 0, s>>>(C, ldc, A, lda, B, ldb, (int)M, (int)N, (int)K, fmt);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
@@ -973,7 +1082,7 @@ gir_status lu_panel_only(float* W, int64_t ldw, int64_t m, int w, int* ipiv, int
         if (plan.panel_smem_budget < 4) plan.panel_smem_budget = 4;
         plan.forced_cluster = 1;
     }
-    PanelTail tail = {nullptr, 0, 0, 0, 0, 0, 0, nullptr, 0};
+    PanelTail tail = {nullptr, 0, 0, 0, 0, 0, 0, nullptr, 0, 0, 0, 0};
     return launch_panel(W, ldw, 0, m, w, ipiv, flags, plan, tail, s);
 }
 
@@ -993,9 +1102,13 @@ gir_status lu_prepare(LUPlan& plan) {
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)trsm_band_smem<16>()));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_band_smem<64>()));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_band_smem<16>()));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)trsm_band_smem<64>()));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_swap_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(PERM_MAXN * sizeof(int))));
@@ -1037,6 +1150,8 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
     const int NB = plan.nb;
     const int64_t ldut = NB;
     if (NB > PERM_MAXK || NB > TB_MAXNB) return GIR_UNSUPPORTED;
+    if (plan.fp8 && (NB != FP8_TILE || w != 32)) return GIR_UNSUPPORTED;
+    const bool fp8 = plan.fp8 != 0;
     SwapScratch sw;
     // The critical path (panels, interchanges, next-block update) runs on a highest-priority
     // stream so that its small kernels get SMs ahead of the side stream's bulk trailing update.
@@ -1075,12 +1190,22 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
     auto trsm_band = [&](int64_t C0, int64_t NBc, int64_t col0, int64_t col1, bool narrow, cudaStream_t ss) {
         if (col1 <= col0) return;
         if (narrow) {
-            count_launch(), k_trsm_band<16><<<(unsigned)((col1 - col0 + 15) / 16), 256, trsm_band_smem<16>(), ss>>>(
-                LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
+            if (fp8)
+                count_launch(), k_trsm_band<16, false><<<(unsigned)((col1 - col0 + 15) / 16), 256, trsm_band_smem<16>(), ss>>>(
+                    LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
+            else
+                count_launch(), k_trsm_band<16, true><<<(unsigned)((col1 - col0 + 15) / 16), 256, trsm_band_smem<16>(), ss>>>(
+                    LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
         } else {
-            count_launch(), k_trsm_band<64><<<(unsigned)((col1 - col0 + 63) / 64), 256, trsm_band_smem<64>(), ss>>>(
-                LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
+            if (fp8)
+                count_launch(), k_trsm_band<64, false><<<(unsigned)((col1 - col0 + 63) / 64), 256, trsm_band_smem<64>(), ss>>>(
+                    LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
+            else
+                count_launch(), k_trsm_band<64, true><<<(unsigned)((col1 - col0 + 63) / 64), 256, trsm_band_smem<64>(), ss>>>(
+                    LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
         }
+        // FP8: U12 of these columns rounded 128 x 128 tile by tile (LU, UT)
+        if (fp8) quantize_tiles(W, ldw, LU, ldl, UT, ldut, C0, NBc, col0, col1 - col0, TILE_FULL, ss);
     };
     for (int64_t C0 = 0; C0 < n && st == GIR_OK; C0 += NB) {
         const int64_t NBc = gmin<int64_t>(NB, n - C0);
@@ -1093,7 +1218,12 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             {
                 // the panel kernel also stores the u_f panel, applies its interchanges to the
                 // block's later columns of W and earlier columns of LU, and solves for U12
-                PanelTail tail = {LU, ldl, fmt, c0 + wc, Cend, C0, c0, UT + (c0 - C0), ldut};
+                PanelTail tail = {LU, ldl, fmt, c0 + wc, Cend, C0, c0, UT + (c0 - C0), ldut, 0, 0, 1};
+                if (fp8) {
+                    // inside an FP8 block column everything stays FP32 in W: the earlier panels'
+                    // multipliers take the interchanges there, and U12 is solved unrounded
+                    tail = PanelTail{nullptr, ldl, fmt, c0 + wc, Cend, 0, 0, nullptr, 0, C0, c0, 2};
+                }
                 GIR_TRY(launch_panel(W, ldw, c0, n, wc, ipiv, flags, plan, tail, s));
             }
             trace_end(t_, "lu panel", s);
@@ -1106,12 +1236,22 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             if (c0 + wc < Cend) {
                 int64_t ncols = Cend - (c0 + wc);
                 t_ = trace_begin(s);
-                GIR_TRY(gemm_sub(W + (c0 + wc) * ldw + (c0 + wc), ldw, LU + (c0 + wc) * ldl + c0, ldl,
-                                 LU + c0 * ldl + (c0 + wc), ldl, UT + (c0 + wc) * ldut + (c0 - C0), ldut,
-                                 n - (c0 + wc), ncols, wc, fmt, plan, flags, s));
+                if (fp8) {
+                    GIR_TRY(gemm_sub_f32(W + (c0 + wc) * ldw + (c0 + wc), ldw, W + (c0 + wc) * ldw + c0, ldw,
+                                         W + c0 * ldw + (c0 + wc), ldw, n - (c0 + wc), ncols, wc, s));
+                } else {
+                    GIR_TRY(gemm_sub(W + (c0 + wc) * ldw + (c0 + wc), ldw, LU + (c0 + wc) * ldl + c0, ldl,
+                                     LU + c0 * ldl + (c0 + wc), ldl, UT + (c0 + wc) * ldut + (c0 - C0), ldut,
+                                     n - (c0 + wc), ncols, wc, fmt, plan, flags, s));
+                }
                 trace_end(t_, "lu inner gemm", s);
                 GIR_TRY(debug_check("inner gemm", C0, c0, flags, s));
             }
+        }
+        if (fp8) {
+            // the block column's factors, rounded to e4m3 tile by tile: L below the diagonal and U11
+            quantize_tiles(W, ldw, LU, ldl, nullptr, 0, C0, n - C0, C0, NBc, TILE_LOWER, s);
+            quantize_tiles(W, ldw, LU, ldl, nullptr, 0, C0, NBc, C0, NBc, TILE_UPPER, s);
         }
         // the previous block's (b) part touches the trailing W columns and reads L rows of that
         // block: it must finish before this block's interchanges move those rows

@@ -11,6 +11,8 @@ struct LUPlan {
     int64_t panel_smem_budget = 200 * 1024;  // panel rows held per CTA, bytes
     int max_cluster = 16;             // CTAs per panel cluster (non-portable size)
     int forced_cluster = 0;           // test hook: cluster size fixed by the budget alone
+    int fp8 = 0;                      // FP8-E4M3 model: 128-wide FP32 block columns, operands
+                                      // rounded per 128 x 128 tile (nb must be 128)
 };
 
 gir_status lu_prepare(LUPlan& plan);

@@ -199,3 +199,51 @@ def test_small_eig(G, d, largest):
     want = allm[::-1][:P.shape[1]] if largest else allm[:P.shape[1]]
     assert np.allclose(np.sort(mags), np.sort(want), rtol=1e-8, atol=1e-12)
     assert abs(P.shape[1] - k) <= 1
+
+
+def _tile_scale(vmax):
+    """Power-of-two s with vmax * s in (224, 448] (the block scale of the FP8 model)."""
+    return 1.0 if vmax == 0 else 2.0 ** np.floor(np.log2(448.0 / vmax))
+
+
+def _assert_e4m3_tiles(X, mask, row0=0, col0=0):
+    """Every 128 x 128 tile (global grid) of X restricted to mask holds e4m3 values times the
+    reciprocal of a power-of-two scale derived from the tile's largest stored magnitude."""
+    m, n = X.shape
+    for r in range(0, m, 128):
+        for c in range(0, n, 128):
+            blk = X[r:r + 128, c:c + 128][mask[r:r + 128, c:c + 128]]
+            if blk.size == 0:
+                continue
+            s = _tile_scale(np.abs(blk).max())
+            for ss in (s, 2 * s):        # a tile maximum that rounded down to 224 / s also fits 2 s
+                if np.array_equal(round_to(blk * ss, "e4m3"), blk * ss):
+                    break
+            else:
+                raise AssertionError(f"tile ({r}, {c}) is not e4m3 under scale {s}")
+
+
+@pytest.mark.parametrize("n", [200, 300, 517])
+def test_factor_properties_fp8(G, n):
+    """FP8-E4M3 u_f with 128 x 128 power-of-two tile scales: the factors satisfy the u_f backward
+    error bound of the oracle's block model (128-wide FP32 block columns), |L| <= 1, and every
+    stored tile is an e4m3 tile under its scale."""
+    A = randsvd(n, 1e2, seed=n)
+    F, Fg = _gpu_factors(G, A, "e4m3")
+    Fo = olu.lu_block(A, "e4m3", w=32)
+    assert np.all(Fg.R == 1.0) and np.all(Fg.S == 1.0) and Fg.mu == 1.0
+    E = np.abs(A[Fg.perm] - Fg.L @ Fg.U).max() / (np.abs(Fg.L) @ np.abs(Fg.U)).max()
+    Eo = np.abs(A[Fo.perm] - Fo.L @ Fo.U).max() / (np.abs(Fo.L) @ np.abs(Fo.U)).max()
+    u8 = UNIT_ROUNDOFF["e4m3"]
+    assert E <= 8 * u8 and E <= 4 * Eo + u8
+    assert np.abs(np.tril(Fg.L, -1)).max() <= 1.0
+    strict = np.tril(np.ones((n, n), bool), -1)
+    _assert_e4m3_tiles(np.tril(Fg.L, -1), strict)
+    # U: the diagonal tiles (upper part) and the tiles right of them are rounded separately
+    for c0 in range(0, n, 128):
+        c1 = min(n, c0 + 128)
+        top = Fg.U[c0:c1, c0:c1]
+        _assert_e4m3_tiles(top, np.triu(np.ones_like(top, bool)))
+        if c1 < n:
+            _assert_e4m3_tiles(Fg.U[c0:c1, c1:], np.ones((c1 - c0, n - c1), bool))
+    F.close()

@@ -335,3 +335,14 @@ def test_autotune_and_tuned_batch(pkg):
     assert "class 11:" in pkg.tune_report()
     for A, b, x in zip(As, bs, xs):
         assert normwise_berr(A, x.cpu().numpy(), b) <= 2 * 2.0 ** -53 * 4
+
+
+@pytest.mark.parametrize("n,kappa,m", [(256, 10.0, 30), (300, 30.0, 50)])
+def test_fp8_solve_parity(pkg, n, kappa, m):
+    """u_f = FP8-E4M3 (tile-scaled) with FP64 working precision and residual: the refinement reaches
+    the FP64 backward error like the oracle, with iteration counts within 10%."""
+    A = randsvd(n, kappa, seed=1)
+    b = A @ normal_vector(n, 2)
+    x, info, xo, io = run_both(pkg, A, b, "e4m3", "fp64", "fp64", m, 10, 1e-8, target=1e-15)
+    assert_parity(A, b, x, info, xo, io, "fp64")
+    assert normwise_berr(A, x, b) <= 1e-15
