@@ -141,6 +141,12 @@ gir_status gir_autotune(const int64_t* n, int count, void* stream);
  * buf (host, buflen bytes, NUL-terminated) and returns the full length needed. */
 int gir_tune_report(char* buf, int buflen);
 
+/* Gradient of a loss L(x) of x = A^-1 b with respect to A, given lambda = A^-T dL/dx from
+ * gir_solve_adjoint: dA = -lambda x^T (n x n, row-major, leading dimension ldda >= n). All
+ * device pointers; enqueued on stream. Not in the paper (the differentiable-solve pattern). */
+gir_status gir_adjoint_grad_a(const double* lambda, const double* x, int64_t n, double* dA, int64_t ldda,
+                              void* stream);
+
 void gir_free(gir_handle* h);
 const char* gir_status_string(gir_status s);
 int64_t gir_handle_n(const gir_handle* h);

@@ -763,6 +763,12 @@ gir_status gir_gemv(const double* A, int64_t n, int64_t lda, const double* v, do
     return st;
 }
 
+gir_status gir_adjoint_grad_a(const double* lambda, const double* x, int64_t n, double* dA, int64_t ldda,
+                              void* stream) {
+    if (!lambda || !x || !dA || n < 1 || ldda < n) return GIR_INVALID_ARG;
+    return launch_outer(lambda, x, n, -1.0, dA, ldda, (cudaStream_t)stream);
+}
+
 gir_status gir_export_factors(const gir_handle* h, float* LU, int32_t* ipiv, double* R, double* S, double* mu,
                               void* stream) {
     if (!h) return GIR_INVALID_ARG;

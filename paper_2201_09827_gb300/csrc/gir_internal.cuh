@@ -148,6 +148,9 @@ gir_status launch_gemm_nn(const double* X, int64_t ldx, int p, const double* Cf,
                           double* Y, int64_t ldy, double alpha, double beta, int64_t n, int round32,
                           cudaStream_t s);
 gir_status launch_norm2(const double* x, int64_t n, double* out, double* scratch, cudaStream_t s);
+// G = alpha u v^T (n x n, row-major)
+gir_status launch_outer(const double* u, const double* v, int64_t n, double alpha, double* G, int64_t ldg,
+                        cudaStream_t s);
 gir_status launch_norminf(const double* x, int64_t n, double* out, cudaStream_t s);
 gir_status launch_matrix_norminf(const double* A, int64_t n, int64_t lda, double* out, double* scratch,
                                  cudaStream_t s);

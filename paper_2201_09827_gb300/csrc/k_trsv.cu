@@ -276,6 +276,169 @@ __global__ void k_minv_post_t(const float2* __restrict__ y, const int* __restric
     }
 }
 
+// ------------------------------------------------------------------ forward-order solves
+// M^-1 applies L then U in their natural orders (TRANS = false). Same ticketed scheme and
+// 64-row blocks as k_trsv, organised for throughput: 256 threads, row r = tid / 4 of the block
+// and quarter q = tid % 4 of its columns (16 each). The off-diagonal tiles do not depend on y,
+// so they stream through a 4-stage cp.async ring (each thread copies and later reads only its
+// own 32 bytes of a tile) and a CTA that falls behind the published blocks catches up at
+// streaming speed; the four lanes of a row reduce by shuffles and all hold the row's
+// accumulator, so each tile costs one CTA barrier (for the shared block of y).
+constexpr int TF_STAGES = 4;
+constexpr int TF_AHEAD = TF_STAGES - 1;
+
+__device__ __forceinline__ void tf_cp_async16(void* smem, const void* gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tf_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void tf_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <bool LOWER>
+__global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ LU, int64_t ldl, int fmt,
+                                                  const float2* __restrict__ D, int64_t n, int nblk,
+                                                  const double* __restrict__ zin64, const float2* __restrict__ zin_ff,
+                                                  float2* __restrict__ yout, unsigned long long* __restrict__ ticket_ctr,
+                                                  unsigned long long base, int* __restrict__ abort_flag,
+                                                  int* __restrict__ flags) {
+    __shared__ __align__(16) uint4 ring[TF_STAGES][2][256];   // [stage][chunk][thread]
+    __shared__ float2 yj[2][TB + 2];                          // padded by one entry per 32
+    __shared__ float2 accs[TB + 2];
+    __shared__ int s_ticket, s_abort;
+    unsigned long long* ybits = reinterpret_cast<unsigned long long*>(yout);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_ticket = (int)(atomicAdd(ticket_ctr, 1ULL) - base);
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int t = s_ticket;
+    if (t < 0 || t >= nblk) {
+        if (tid == 0) { atomicOr(flags, DEV_TIMEOUT); atomicExch(abort_flag, 1); }
+        return;
+    }
+    const int I = LOWER ? t : (nblk - 1 - t);
+    const int64_t r0 = (int64_t)I * TB;
+    const int r = tid >> 2, q = tid & 3;
+    const int64_t gi = r0 + r;
+    auto pad = [](int c) { return c + (c >> 5); };
+    float ah = 0.0f, al = 0.0f;
+    if (gi < n) {
+        if (zin64) {
+            const double v = zin64[gi];
+            ah = __double2float_rn(v);
+            al = __double2float_rn(v - (double)ah);
+        } else {
+            const float2 v = zin_ff[gi];
+            ah = v.x;
+            al = v.y;
+        }
+    }
+    const int ndep = LOWER ? I : (nblk - 1 - I);
+    // this thread's 16 entries of the diagonal-block inverse, loaded now: the product with them
+    // follows the last dependency and is on the critical path of the solve
+    float4 dreg[8];
+    {
+        const float4* drow = reinterpret_cast<const float4*>(D + ((int64_t)I * TB + r) * TB + q * 16);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dreg[k] = drow[k];
+    }
+    auto dep_block = [&](int step) { return LOWER ? step : (nblk - 1 - step); };
+    auto issue = [&](int step, int st) {
+        const int64_t c0 = (int64_t)dep_block(step) * TB + q * 16;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t cc = c0 + 8 * k;
+            int bytes = 0;
+            if (gi < n && cc < n) bytes = (int)(2 * gmin<int64_t>(8, n - cc));
+            const uint16_t* src = bytes ? LU + gi * ldl + cc : LU;
+            tf_cp_async16(&ring[st][k][tid], src, bytes);
+        }
+    };
+    auto wait_block = [&](int J, int buf) {
+        if (tid < TB) {
+            const int64_t gc = (int64_t)J * TB + tid;
+            unsigned long long v = 0ull;
+            if (gc < n) {
+                long long spins = 0;
+                while ((v = ld_relaxed_u64(ybits + gc)) == Y_EMPTY) {
+                    if (((spins & 1023) == 0) && ld_acquire(abort_flag)) { s_abort = 1; break; }
+                    if (++spins > SPIN_LIMIT) {
+                        atomicOr(flags, DEV_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+            }
+            yj[buf][pad(tid)] = make_float2(__uint_as_float((unsigned)(v & 0xffffffffull)),
+                                            __uint_as_float((unsigned)(v >> 32)));
+        }
+    };
+    auto quad_reduce = [&](float& sh, float& sl) {
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            ff_acc_add(sh, sl, oh, ol);
+        }
+    };
+#pragma unroll
+    for (int p = 0; p < TF_AHEAD; ++p) {
+        if (p < ndep) issue(p, p);
+        tf_cp_commit();
+    }
+    for (int step = 0; step < ndep; ++step) {
+        if (step + TF_AHEAD < ndep) issue(step + TF_AHEAD, (step + TF_AHEAD) % TF_STAGES);
+        tf_cp_commit();
+        tf_cp_wait<TF_AHEAD>();
+        const int buf = step & 1;
+        wait_block(dep_block(step), buf);
+        __syncthreads();
+        if (s_abort) break;
+        const int st = step % TF_STAGES;
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint4 v = ring[st][k][tid];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int c = q * 16 + 8 * k + 2 * m;
+                const float2 y0 = yj[buf][pad(c)], y1 = yj[buf][pad(c + 1)];
+                ff_acc_prod1(sh, sl, uf_to_float((uint16_t)(w[m] & 0xffffu), fmt), y0.x, y0.y);
+                ff_acc_prod1(sh, sl, uf_to_float((uint16_t)(w[m] >> 16), fmt), y1.x, y1.y);
+            }
+        }
+        quad_reduce(sh, sl);
+        ff_acc_add(ah, al, -sh, -sl);
+        const ff ns = ff_norm(ah, al);
+        ah = ns.h;
+        al = ns.l;
+    }
+    tf_cp_wait<0>();
+    // y_I = D_I acc
+    if (q == 0) accs[pad(r)] = make_float2(ah, al);
+    __syncthreads();
+    float ph = 0.0f, pl = 0.0f;
+    {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 d = dreg[k];   // two float-float entries
+            const float2 a0 = accs[pad(q * 16 + 2 * k)], a1 = accs[pad(q * 16 + 2 * k + 1)];
+            ff_acc_prod2(ph, pl, d.x, d.y, a0.x, a0.y);
+            ff_acc_prod2(ph, pl, d.z, d.w, a1.x, a1.y);
+        }
+        quad_reduce(ph, pl);
+    }
+    if (q == 0 && gi < n) {
+        const ff ns = ff_norm(ph, pl);
+        st_relaxed_u64(ybits + gi, s_abort ? pack_ff(0.0f, 0.0f) : pack_ff(ns.h, ns.l));
+    }
+}
+
 // ------------------------------------------------------------------ host side
 gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, cudaStream_t s) {
     st.n = n;
@@ -308,14 +471,29 @@ static gir_status run_trsv(TrsvState& st, const float2* D, const double* z64, co
     return GIR_OK;
 }
 
+template <bool LOWER>
+static gir_status run_trsv_fwd(TrsvState& st, const float2* D, const double* z64, const float2* zff, float2* y,
+                               int* flags, cudaStream_t s) {
+    unsigned long long base = st.tickets;
+    st.tickets += (unsigned long long)st.nblk;
+    GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
+    const int tslot = trace_begin(s);
+    count_launch(), k_trsv_fwd<LOWER><<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, st.nblk, z64, zff, y,
+                                                           st.ticket_ctr, base, st.abort_flag, flags);
+    trace_end(tslot, "trsv", s);
+    st.calls++;
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
 gir_status apply_minv(TrsvState& st, const double* w, double* out, const double* R, const double* S, double mu,
                       int trans, int round32, int* flags, cudaStream_t s) {
     const int64_t n = st.n;
     const int g = (int)gmin<int64_t>((n + 255) / 256, 1024);
     if (!trans) {
         count_launch(), k_minv_pre<<<g, 256, 0, s>>>(w, st.perm, R, n, st.z);
-        GIR_TRY((run_trsv<true, false>(st, st.DL, st.z, nullptr, st.y1, flags, s)));
-        GIR_TRY((run_trsv<false, false>(st, st.DU, nullptr, st.y1, st.y2, flags, s)));
+        GIR_TRY((run_trsv_fwd<true>(st, st.DL, st.z, nullptr, st.y1, flags, s)));
+        GIR_TRY((run_trsv_fwd<false>(st, st.DU, nullptr, st.y1, st.y2, flags, s)));
         count_launch(), k_minv_post<<<g, 256, 0, s>>>(st.y2, S, mu, n, round32, out);
     } else {
         count_launch(), k_minv_pre_t<<<g, 256, 0, s>>>(w, S, n, st.z);

@@ -345,4 +345,34 @@ gir_status launch_matrix_norminf(const double* A, int64_t n, int64_t lda, double
     return launch_norminf(scratch, n, out, s);
 }
 
+
+// G = alpha * u v^T (n x n, row-major, leading dimension ldg): the gradient dA = -lambda x^T of a
+// loss of x = A^-1 b. Each CTA writes whole rows with 16-byte stores where the row pitch allows.
+__global__ void __launch_bounds__(256) k_outer(const double* __restrict__ u, const double* __restrict__ v, int64_t n,
+                                               double alpha, double* __restrict__ G, int64_t ldg) {
+    const bool vec = ((ldg & 1) == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(v) & 15) == 0);
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const double ui = alpha * u[i];
+        double* g = G + i * ldg;
+        if (vec) {
+            for (int64_t j = 2 * (int64_t)threadIdx.x; j + 1 < n; j += 2 * (int64_t)blockDim.x) {
+                const double2 vv = *reinterpret_cast<const double2*>(v + j);
+                *reinterpret_cast<double2*>(g + j) = make_double2(ui * vv.x, ui * vv.y);
+            }
+            if ((n & 1) && threadIdx.x == 0) g[n - 1] = ui * v[n - 1];
+        } else {
+            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) g[j] = ui * v[j];
+        }
+    }
+}
+
+gir_status launch_outer(const double* u, const double* v, int64_t n, double alpha, double* G, int64_t ldg,
+                        cudaStream_t s) {
+    const int g = (int)gmin<int64_t>(n, 152 * 16);
+    count_launch(), k_outer<<<g, 256, 0, s>>>(u, v, n, alpha, G, ldg);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
 }  // namespace gir

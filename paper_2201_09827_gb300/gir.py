@@ -49,6 +49,7 @@ SYMBOLS = {
                                   C.c_void_p]),
     "gir_autotune": (C.c_int, [C.POINTER(C.c_int64), C.c_int, C.c_void_p]),
     "gir_tune_report": (C.c_int, [C.c_char_p, C.c_int]),
+    "gir_adjoint_grad_a": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
     "gir_free": (None, [C.c_void_p]),
     "gir_status_string": (C.c_char_p, [C.c_int]),
     "gir_handle_n": (C.c_int64, [C.c_void_p]),
@@ -433,8 +434,8 @@ def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False):
 class GirSolve(torch.autograd.Function):
     """x = A^-1 b by RGMRES-IR; backward solves A^T lambda = g with the same factors.
 
-    Gradients: db = lambda, dA = -lambda x^T (the outer product is formed by torch as
-    plumbing of the autograd graph; the adjoint solve itself runs in the library).
+    Gradients: db = lambda, dA = -lambda x^T, both computed by the library (the adjoint solve
+    and gir_adjoint_grad_a).
     """
 
     @staticmethod
@@ -452,5 +453,11 @@ class GirSolve(torch.autograd.Function):
         lam, info = ctx.F.solve_adjoint(A, g.contiguous())
         if info.status not in (GIR_OK, GIR_NOT_CONVERGED):
             raise GirError(info.status, "gir_solve_adjoint")
-        dA = -torch.outer(lam, x) if ctx.needs_input_grad[0] else None
+        dA = None
+        if ctx.needs_input_grad[0]:
+            n = x.shape[0]
+            dA = torch.empty((n, n), dtype=torch.float64, device=x.device)
+            st = load().gir_adjoint_grad_a(_ptr(lam), _ptr(x), n, _ptr(dA), n, _stream(None))
+            if st != GIR_OK:
+                raise GirError(st, "gir_adjoint_grad_a")
         return dA, lam, None

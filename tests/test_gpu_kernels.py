@@ -247,3 +247,19 @@ def test_factor_properties_fp8(G, n):
         if c1 < n:
             _assert_e4m3_tiles(Fg.U[c0:c1, c1:], np.ones((c1 - c0, n - c1), bool))
     F.close()
+
+
+@pytest.mark.parametrize("n,ld", [(1, 1), (7, 9), (300, 300), (1001, 1004)])
+def test_adjoint_grad_a(G, n, ld):
+    """dA = -lambda x^T: one FP64 product per entry, so bit-identical to numpy's outer product."""
+    rng = np.random.default_rng(n)
+    lam, x = rng.standard_normal(n), rng.standard_normal(n)
+    dA = torch.full((n, ld), 7.0, dtype=torch.float64, device="cuda")
+    lib = G.load()
+    lam_d, x_d = cuda(lam), cuda(x)
+    st = lib.gir_adjoint_grad_a(lam_d.data_ptr(), x_d.data_ptr(), n, dA.data_ptr(), ld, None)
+    torch.cuda.synchronize()
+    assert st == 0
+    got = dA.cpu().numpy()
+    assert np.array_equal(got[:, :n], -np.outer(lam, x))
+    assert np.all(got[:, n:] == 7.0)
