@@ -65,6 +65,10 @@ struct gir_handle {
     double* Ctmp = nullptr;  // n x KMAX
     double* Utmp = nullptr;  // n x KMAX
     double* vtmp = nullptr;  // n
+    float* Ahi = nullptr;    // float-float split of A (A_hi + A_lo), n x ldf, for the Arnoldi products
+    float* Alo = nullptr;
+    int64_t ldf = 0;
+    float* vsplit = nullptr;  // 2 * ldf
     double* r = nullptr;     // n (GCRO-DR residual)
     double* dvec = nullptr;  // n (GCRO-DR solution)
     double* cvec = nullptr;  // n (preconditioned rhs)
@@ -134,7 +138,7 @@ void free_handle_on(gir_handle* h, cudaStream_t s) {
     void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.perm, h->trsv.z, h->trsv.y1,
                     h->trsv.y2, h->trsv.ready, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
-                    h->scratch, h->st, h->qh, h->dsc, h->dflags};
+                    h->scratch, h->st, h->qh, h->dsc, h->dflags, h->Ahi, h->Alo, h->vsplit};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     if (h->hsc) cudaFreeHost(h->hsc);
@@ -257,9 +261,17 @@ gir_status flags_status(int f) {
 }
 
 // w = M^-1 A v (trans: M^-T A^T v), rounded to u
+// A v for the correction equation: float-float from the split of A for A~ = M^-1 A (the triangular
+// solves are float-float too); FP64 for the transposed operator of the adjoint solve
+gir_status launch_op_gemv(gir_handle* h, const double* A, int64_t lda, const double* v, double* w, int trans,
+                          cudaStream_t s) {
+    if (!trans) return launch_gemv_ff(h->Ahi, h->Alo, h->ldf, h->n, v, w, h->vsplit, s);
+    return launch_gemv(A, h->n, lda, v, w, trans, h->scratch, s);
+}
+
 gir_status apply_atilde(gir_handle* h, const double* A, int64_t lda, const double* v, double* w, int trans,
                         cudaStream_t s) {
-    GIR_TRY(launch_gemv(A, h->n, lda, v, h->vtmp, trans, h->scratch, s));
+    GIR_TRY(launch_op_gemv(h, A, lda, v, h->vtmp, trans, s));
     return apply_minv(h->trsv, h->vtmp, w, h->scaled ? h->R : nullptr, h->scaled ? h->S : nullptr, h->mu, trans,
                       h->round32, h->dflags, s);
 }
@@ -275,7 +287,7 @@ gir_status arnoldi_step(gir_handle* h, const double* A, int64_t lda, int trans, 
     double* vj = V(h, j);
     double* w = V(h, j + 1);
     { int tslot_ = trace_begin(s);
-    GIR_TRY(launch_gemv(A, n, lda, vj, h->vtmp, trans, h->scratch, s));
+    GIR_TRY(launch_op_gemv(h, A, lda, vj, h->vtmp, trans, s));
     trace_end(tslot_, "gemv", s); }
     { int tslot_ = trace_begin(s);
     GIR_TRY(apply_minv_h(h, h->vtmp, w, trans, s));
@@ -636,6 +648,10 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     ALLOC(h->Ctmp, (size_t)n * KMAX);
     ALLOC(h->Utmp, (size_t)n * KMAX);
     ALLOC(h->vtmp, n);
+    h->ldf = (n + 3) / 4 * 4;
+    ALLOC(h->Ahi, (size_t)n * h->ldf);
+    ALLOC(h->Alo, (size_t)n * h->ldf);
+    ALLOC(h->vsplit, (size_t)2 * h->ldf);
     ALLOC(h->r, n);
     ALLOC(h->dvec, n);
     ALLOC(h->cvec, n);
@@ -696,8 +712,30 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
         st = lu_scale_quantize(A, n, lda, params->uf, h->R, h->S, &mu, W, ldw, colmax, h->dflags, s);
         h->mu = mu;
     }
+    // the float-float split of A for the correction solves, on a low-priority stream beside the
+    // (latency-bound) factorization, on few CTAs so that the panel clusters still find free SMs
+    cudaStream_t s_aux = nullptr;
+    cudaEvent_t ev_aux = nullptr;
+    if (st == GIR_OK) {
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        if (cudaStreamCreateWithPriority(&s_aux, cudaStreamNonBlocking, lo_prio) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_aux, cudaEventDisableTiming) != cudaSuccess) {
+            st = GIR_CUDA_ERROR;
+        } else {
+            cudaEventRecord(ev_aux, s);
+            cudaStreamWaitEvent(s_aux, ev_aux, 0);
+            st = launch_split_matrix(A, n, lda, h->Ahi, h->Alo, h->ldf, 24, s_aux);
+            cudaEventRecord(ev_aux, s_aux);
+        }
+    }
     if (st == GIR_OK)
         st = lu_factor(W, ldw, h->LU, h->ldl, h->ipiv, h->trsv.perm, n, h->fmt, h->plan, UT, h->dflags, s);
+    if (ev_aux) {
+        cudaStreamWaitEvent(s, ev_aux, 0);
+        cudaEventDestroy(ev_aux);
+    }
+    if (s_aux) cudaStreamDestroy(s_aux);
     if (st == GIR_OK) st = trsv_setup(h->trsv, h->LU, h->ldl, n, h->fmt, s);
     cudaFreeAsync(W, s);
     cudaFreeAsync(colmax, s);

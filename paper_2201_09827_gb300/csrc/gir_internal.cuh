@@ -148,6 +148,14 @@ gir_status launch_gemm_nn(const double* X, int64_t ldx, int p, const double* Cf,
                           double* Y, int64_t ldy, double alpha, double beta, int64_t n, int round32,
                           cudaStream_t s);
 gir_status launch_norm2(const double* x, int64_t n, double* out, double* scratch, cudaStream_t s);
+// w = A v in float-float from the FP32 split A = A_hi + A_lo (leading dimension ldf, a multiple
+// of 4; 16-byte aligned); vsplit: scratch of 2 * ceil4(n) floats
+// A_hi = RN32(A), A_lo = RN32(A - A_hi) (ldf: row pitch of the FP32 halves, even), on at most
+// max_ctas CTAs
+gir_status launch_split_matrix(const double* A, int64_t n, int64_t lda, float* Ah, float* Al, int64_t ldf,
+                               int max_ctas, cudaStream_t s);
+gir_status launch_gemv_ff(const float* Ah, const float* Al, int64_t ldf, int64_t n, const double* v, double* w,
+                          float* vsplit, cudaStream_t s);
 // G = alpha u v^T (n x n, row-major)
 gir_status launch_outer(const double* u, const double* v, int64_t n, double alpha, double* G, int64_t ldg,
                         cudaStream_t s);

@@ -368,37 +368,76 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
         const bool p_safe = div_safe(piv);
         bv = -1.0f;
         bi = NONE;
-        for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
-            const int g = g0 + lr;
-            float* row = tile + lr * TS;
-            if (g == j) {
+        // rows in pairs (lr, lr + PANEL_THREADS): the two rows' quotient and update chains are
+        // independent and interleave
+        for (int lr0 = tid; lr0 < myrows; lr0 += 2 * PANEL_THREADS) {
+            const int lr1 = lr0 + PANEL_THREADS;
+            const bool has1 = lr1 < myrows;
+            float* rowA = tile + lr0 * TS;
+            float* rowB = tile + (has1 ? lr1 : lr0) * TS;
+            const int gA = g0 + lr0, gB = g0 + lr1;
+            if (gA == j) {
 #pragma unroll
-                for (int c = 0; c < WC; ++c) row[c] = pc[c];
-            } else if (g == pr) {
+                for (int c = 0; c < WC; ++c) rowA[c] = pc[c];
+            } else if (gA == pr) {
 #pragma unroll
-                for (int c = 0; c < WC; ++c) row[c] = rj[c];
+                for (int c = 0; c < WC; ++c) rowA[c] = rj[c];
             }
-            if (g > j) {
-                const float l = (piv != 0.0f) ? div_rn(row[j], piv, rp, p_safe) : 0.0f;
-                row[j] = l;
-                float nv = 0.0f;   // the updated entry of column j + 1
+            if (has1) {
+                if (gB == j) {
 #pragma unroll
-                for (int cb = 0; cb < WC; cb += 8) {
-                    if (cb + 7 > j) {
+                    for (int c = 0; c < WC; ++c) rowB[c] = pc[c];
+                } else if (gB == pr) {
 #pragma unroll
-                        for (int c = cb; c < cb + 8; ++c) {
-                            if (c > j) {
-                                const float t = fmaf(-l, pc[c], row[c]);
-                                row[c] = t;
-                                if (c == j + 1) nv = t;
-                            }
+                    for (int c = 0; c < WC; ++c) rowB[c] = rj[c];
+                }
+            }
+            const bool upA = gA > j, upB = has1 && gB > j;
+            if (!upA && !upB) continue;
+            // quotients: Markstein's correction of x RN(1/p) where it is exact, else the library
+            const float xA = rowA[j], xB = rowB[j];
+            float lA = 0.0f, lB = 0.0f;
+            if (piv != 0.0f) {
+                const float qA = xA * rp, qB = xB * rp;
+                lA = fmaf(fmaf(-qA, piv, xA), rp, qA);
+                lB = fmaf(fmaf(-qB, piv, xB), rp, qB);
+                const bool okA = p_safe && (div_safe(xA) || xA == 0.0f);
+                const bool okB = p_safe && (div_safe(xB) || xB == 0.0f);
+                if (xA == 0.0f) lA = __int_as_float((__float_as_int(xA) ^ __float_as_int(piv)) & (int)0x80000000);
+                if (xB == 0.0f) lB = __int_as_float((__float_as_int(xB) ^ __float_as_int(piv)) & (int)0x80000000);
+                if (!okA) lA = __fdiv_rn(xA, piv);
+                if (!okB) lB = __fdiv_rn(xB, piv);
+            }
+            if (!upA) lA = 0.0f;
+            if (!upB) lB = 0.0f;
+            if (upA) rowA[j] = lA;
+            if (upB) rowB[j] = lB;
+            float nvA = 0.0f, nvB = 0.0f;   // the updated entries of column j + 1
+#pragma unroll
+            for (int cb = 0; cb < WC; cb += 8) {
+                if (cb + 7 > j) {
+#pragma unroll
+                    for (int c = cb; c < cb + 8; ++c) {
+                        if (c > j) {
+                            const float tA = fmaf(-lA, pc[c], rowA[c]);
+                            const float tB = fmaf(-lB, pc[c], rowB[c]);
+                            if (upA) rowA[c] = tA;
+                            if (upB) rowB[c] = tB;
+                            if (c == j + 1) { nvA = tA; nvB = tB; }
                         }
                     }
                 }
-                if (next) {
-                    float v = fabsf(nv);
+            }
+            if (next) {
+                if (upA) {
+                    float v = fabsf(nvA);
                     if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
-                    argmax_merge(bv, bi, v, g);
+                    argmax_merge(bv, bi, v, gA);
+                }
+                if (upB) {
+                    float v = fabsf(nvB);
+                    if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
+                    argmax_merge(bv, bi, v, gB);
                 }
             }
         }

@@ -375,4 +375,118 @@ gir_status launch_outer(const double* u, const double* v, int64_t n, double alph
     return GIR_OK;
 }
 
+
+// ------------------------------------------------------------------ float-float A v
+// w = A v with A held as two FP32 matrices (A_hi = RN32(a), A_lo = RN32(a - A_hi), so
+// A_hi + A_lo carries 48 significand bits of each FP64 entry) and v split the same way, in
+// float-float arithmetic: exact products by FMA (TwoProduct) accumulated with TwoSum. The
+// operator M^-1 A of the correction solves is then applied at one precision (the triangular
+// solves are float-float as well), and the matrix-vector product streams 8 bytes per entry at
+// FP32 arithmetic rates instead of being limited by the FP64 pipe.
+__global__ void k_split_ff(const double* __restrict__ v, int64_t n, float* __restrict__ vh, float* __restrict__ vl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = v[i];
+        const float h = __double2float_rn(a);
+        vh[i] = h;
+        vl[i] = __double2float_rn(a - (double)h);
+    }
+}
+
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float ah, float al, float vh, float vl) {
+    const float p = ah * vh;
+    float e = fmaf(ah, vh, -p);
+    e = fmaf(ah, vl, e);
+    e = fmaf(al, vh, e);
+    const float s = sh + p;
+    const float bb = s - sh;
+    const float t = (sh - (s - bb)) + (p - bb);
+    sh = s;
+    sl += t + e;
+}
+
+// one warp per row; ldf % 4 == 0 and 16-byte aligned A_hi, A_lo, vh, vl (float4 loads)
+__global__ void __launch_bounds__(256) k_gemv_ff(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                 int64_t ldf, int64_t n, const float* __restrict__ vh,
+                                                 const float* __restrict__ vl, double* __restrict__ w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t n4 = n >> 2;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps_total) {
+        const float4* rh = reinterpret_cast<const float4*>(Ah + i * ldf);
+        const float4* rl = reinterpret_cast<const float4*>(Al + i * ldf);
+        const float4* xh = reinterpret_cast<const float4*>(vh);
+        const float4* xl = reinterpret_cast<const float4*>(vl);
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll 2
+        for (int64_t j = lane; j < n4; j += 32) {
+            const float4 a = __ldcs(rh + j), b = __ldcs(rl + j);
+            const float4 c = __ldg(xh + j), d = __ldg(xl + j);
+            ff_mac(sh, sl, a.x, b.x, c.x, d.x);
+            ff_mac(sh, sl, a.y, b.y, c.y, d.y);
+            ff_mac(sh, sl, a.z, b.z, c.z, d.z);
+            ff_mac(sh, sl, a.w, b.w, c.w, d.w);
+        }
+        for (int64_t j = n4 * 4 + lane; j < n; j += 32)
+            ff_mac(sh, sl, Ah[i * ldf + j], Al[i * ldf + j], vh[j], vl[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            const float s2 = sh + oh, bb = s2 - sh, t = (sh - (s2 - bb)) + (oh - bb);
+            sh = s2;
+            sl += t + ol;
+        }
+        if (lane == 0) w[i] = (double)sh + (double)sl;
+    }
+}
+
+// A_hi = RN32(A), A_lo = RN32(A - A_hi), row by row (16-byte loads where A allows)
+__global__ void __launch_bounds__(256) k_split_matrix(const double* __restrict__ A, int64_t n, int64_t lda,
+                                                      float* __restrict__ Ah, float* __restrict__ Al, int64_t ldf) {
+    const bool vec = ((lda & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const double* a = A + i * lda;
+        float* h = Ah + i * ldf;
+        float* l = Al + i * ldf;
+        if (vec) {
+            for (int64_t j = 2 * (int64_t)threadIdx.x; j + 1 < n; j += 2 * (int64_t)blockDim.x) {
+                const double2 v = *reinterpret_cast<const double2*>(a + j);
+                const float h0 = __double2float_rn(v.x), h1 = __double2float_rn(v.y);
+                *reinterpret_cast<float2*>(h + j) = make_float2(h0, h1);
+                *reinterpret_cast<float2*>(l + j) =
+                    make_float2(__double2float_rn(v.x - (double)h0), __double2float_rn(v.y - (double)h1));
+            }
+            if ((n & 1) && threadIdx.x == 0) {
+                const float h0 = __double2float_rn(a[n - 1]);
+                h[n - 1] = h0;
+                l[n - 1] = __double2float_rn(a[n - 1] - (double)h0);
+            }
+        } else {
+            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+                const float h0 = __double2float_rn(a[j]);
+                h[j] = h0;
+                l[j] = __double2float_rn(a[j] - (double)h0);
+            }
+        }
+    }
+}
+
+gir_status launch_split_matrix(const double* A, int64_t n, int64_t lda, float* Ah, float* Al, int64_t ldf,
+                               int max_ctas, cudaStream_t s) {
+    count_launch(), k_split_matrix<<<(unsigned)gmin<int64_t>(n, max_ctas), 256, 0, s>>>(A, n, lda, Ah, Al, ldf);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+gir_status launch_gemv_ff(const float* Ah, const float* Al, int64_t ldf, int64_t n, const double* v, double* w,
+                          float* vsplit, cudaStream_t s) {
+    if (n <= 0) return GIR_OK;
+    float* vh = vsplit;
+    float* vl = vsplit + ((n + 3) / 4) * 4;
+    count_launch(), k_split_ff<<<(unsigned)gmin<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(v, n, vh, vl);
+    count_launch(), k_gemv_ff<<<grid_for_rows(n), 256, 0, s>>>(Ah, Al, ldf, n, vh, vl, w);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
 }  // namespace gir
