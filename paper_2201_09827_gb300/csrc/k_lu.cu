@@ -181,6 +181,7 @@ struct PanelShared {
     int wbest_row[2][PANEL_THREADS / 32];
     int piv[WC];                      // panel-relative pivot row of each column
     float top[WC][WC + 1];            // final rows 0..wcols-1 of the panel (L11 below the diagonal)
+    __align__(16) float ubT[WC][8];   // U rows of the current 8-column mini-panel, column-major
     float l11[WC][WC + 1];            // L11 rounded to u_f (strictly lower part), for the U12 solve
     int ext_row[32];                  // distinct pivot rows below the panel's diagonal block
     int mv_dst[64], mv_src[64];       // net row moves of the panel's interchanges
@@ -228,6 +229,50 @@ __device__ __forceinline__ bool div_safe(float v) {
     const uint32_t e = (__float_as_uint(v) >> 23) & 0xffu;
     return e >= 127u - 96u && e <= 127u + 96u;
 }
+// Rank-1 update of one mini-panel chunk [CB, CB + 8) of two rows (columns > j), returning the
+// updated entries of column j + 1; CB is a compile-time start so that only this chunk's code is
+// issued (the caller switches on the warp-uniform j / 8).
+template <int CB>
+__device__ __forceinline__ void chunk_update(float* rowA, float* rowB, const float* pc, float lA, float lB, bool upA,
+                                             bool upB, int j, float& nvA, float& nvB) {
+#pragma unroll
+    for (int c = CB; c < CB + 8; ++c) {
+        if (c > j) {
+            const float tA = fmaf(-lA, pc[c], rowA[c]);
+            const float tB = fmaf(-lB, pc[c], rowB[c]);
+            if (upA) rowA[c] = tA;
+            if (upB) rowB[c] = tB;
+            if (c == j + 1) { nvA = tA; nvB = tB; }
+        }
+    }
+}
+
+__device__ __noinline__ float div_slow(float x, float p) { return __fdiv_rn(x, p); }
+
+// Rank-8 update of one row's columns [CS, WC) by the mini-panel ending at column CS - 1 (its
+// multipliers l, its U rows ubT column-major), in step order; returns the new entry of column CS.
+template <int CS, int WC>
+__device__ __forceinline__ float block_update(float* row, const float (*ubT)[8], const float* l) {
+    float nv = 0.0f;
+#pragma unroll
+    for (int c = CS; c < WC; ++c) {
+        const float4 u0 = *reinterpret_cast<const float4*>(&ubT[c][0]);
+        const float4 u1 = *reinterpret_cast<const float4*>(&ubT[c][4]);
+        float x = row[c];
+        x = fmaf(-l[0], u0.x, x);
+        x = fmaf(-l[1], u0.y, x);
+        x = fmaf(-l[2], u0.z, x);
+        x = fmaf(-l[3], u0.w, x);
+        x = fmaf(-l[4], u1.x, x);
+        x = fmaf(-l[5], u1.y, x);
+        x = fmaf(-l[6], u1.z, x);
+        x = fmaf(-l[7], u1.w, x);
+        row[c] = x;
+        if (c == CS) nv = x;
+    }
+    return nv;
+}
+
 __device__ __forceinline__ float div_rn(float x, float p, float rp, bool p_safe) {
     if (x == 0.0f) return __int_as_float((__float_as_int(x) ^ __float_as_int(p)) & (int)0x80000000);
     if (p_safe && div_safe(x)) {
@@ -320,6 +365,9 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
                 }
             }
         }
+        // the senders have read their tile rows before any thread updates a row (a thread's own
+        // message wait does not cover this CTA's sends to the other CTAs)
+        __syncthreads();
         if (!dead && !pn_mbar_wait(&sh.bar[buf], (uint32_t)((j >> 1) & 1))) {
             dead = true;
             local_flag |= DEV_TIMEOUT;
@@ -363,7 +411,10 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
             pc[4 * k + 2] = v.z;
             pc[4 * k + 3] = v.w;
         }
-        const bool next = j + 1 < wcols;
+        // columns are processed in mini-panels of 8: a pivot step updates only the rest of its
+        // mini-panel; the later columns get the mini-panel's rank-8 update after its last step
+        // (same FP32 operations in the same order as rank-1 updates, far less shared-memory traffic)
+        const bool next = j + 1 < wcols && (j & 7) != 7;
         const float rp = (piv != 0.0f) ? __frcp_rn(piv) : 0.0f;
         const bool p_safe = div_safe(piv);
         bv = -1.0f;
@@ -405,28 +456,20 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
                 const bool okB = p_safe && (div_safe(xB) || xB == 0.0f);
                 if (xA == 0.0f) lA = __int_as_float((__float_as_int(xA) ^ __float_as_int(piv)) & (int)0x80000000);
                 if (xB == 0.0f) lB = __int_as_float((__float_as_int(xB) ^ __float_as_int(piv)) & (int)0x80000000);
-                if (!okA) lA = __fdiv_rn(xA, piv);
-                if (!okB) lB = __fdiv_rn(xB, piv);
+                // rare (operands near the exponent limits): an out-of-line call, so a real branch
+                if (!okA) lA = div_slow(xA, piv);
+                if (!okB) lB = div_slow(xB, piv);
             }
             if (!upA) lA = 0.0f;
             if (!upB) lB = 0.0f;
             if (upA) rowA[j] = lA;
             if (upB) rowB[j] = lB;
             float nvA = 0.0f, nvB = 0.0f;   // the updated entries of column j + 1
-#pragma unroll
-            for (int cb = 0; cb < WC; cb += 8) {
-                if (cb + 7 > j) {
-#pragma unroll
-                    for (int c = cb; c < cb + 8; ++c) {
-                        if (c > j) {
-                            const float tA = fmaf(-lA, pc[c], rowA[c]);
-                            const float tB = fmaf(-lB, pc[c], rowB[c]);
-                            if (upA) rowA[c] = tA;
-                            if (upB) rowB[c] = tB;
-                            if (c == j + 1) { nvA = tA; nvB = tB; }
-                        }
-                    }
-                }
+            switch (j >> 3) {
+                case 0: chunk_update<0>(rowA, rowB, pc, lA, lB, upA, upB, j, nvA, nvB); break;
+                case 1: chunk_update<8>(rowA, rowB, pc, lA, lB, upA, upB, j, nvA, nvB); break;
+                case 2: if (WC > 16) chunk_update<16 % WC>(rowA, rowB, pc, lA, lB, upA, upB, j, nvA, nvB); break;
+                default: if (WC > 16) chunk_update<24 % WC>(rowA, rowB, pc, lA, lB, upA, upB, j, nvA, nvB); break;
             }
             if (next) {
                 if (upA) {
@@ -438,6 +481,50 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
                     float v = fabsf(nvB);
                     if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
                     argmax_merge(bv, bi, v, gB);
+                }
+            }
+        }
+        if ((j & 7) == 7 && j + 1 < wcols) {
+            const int j0 = j - 7;
+            __syncthreads();   // the mini-panel's pivot rows (sh.top) and multipliers are in place
+            // its U rows for the later columns: the pivot rows (as sent, before this mini-panel's
+            // updates) take the updates of the earlier pivot rows in step order
+            if (tid < WC && tid > j) {
+                const int c = tid;
+                float u[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float x = sh.top[j0 + k][c];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (q < k) x = fmaf(-sh.top[j0 + k][j0 + q], u[q], x);
+                    u[k] = x;
+                    sh.top[j0 + k][c] = x;
+                    sh.ubT[c][k] = x;
+                }
+            }
+            __syncthreads();
+            for (int lr = tid; lr < myrows; lr += PANEL_THREADS) {
+                const int g = g0 + lr;
+                float* row = tile + lr * TS;
+                if (g >= j0 && g <= j) {
+                    // a pivot row of this mini-panel: its final U values
+#pragma unroll
+                    for (int c = 0; c < WC; ++c)
+                        if (c > j) row[c] = sh.ubT[c][g - j0];
+                } else if (g > j) {
+                    float l[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) l[q] = row[j0 + q];
+                    float nv = 0.0f;
+                    switch (j >> 3) {   // j + 1 is 8, 16 or 24
+                        case 0: nv = block_update<8, WC>(row, sh.ubT, l); break;
+                        case 1: nv = block_update<(16 < WC ? 16 : WC), WC>(row, sh.ubT, l); break;
+                        default: nv = block_update<(24 < WC ? 24 : WC), WC>(row, sh.ubT, l); break;
+                    }
+                    float v = fabsf(nv);
+                    if (v != v) { local_flag |= DEV_NONFINITE; v = -1.0f; }
+                    argmax_merge(bv, bi, v, g);
                 }
             }
         }

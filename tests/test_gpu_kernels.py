@@ -81,8 +81,11 @@ def panel_oracle(W):
 
 
 @pytest.mark.parametrize("m,w,cluster", [(32, 32, 1), (200, 32, 1), (2000, 32, 2), (2000, 32, 5), (3001, 17, 13),
-                                         (1000, 16, 16), (77, 1, 3), (4096, 7, 8)])
+                                         (1000, 16, 16), (77, 1, 3), (4096, 7, 8),
+                                         (1500, 32, 1), (1400, 16, 1)])
 def test_panel_bitexact(G, m, w, cluster):
+    """Ties in the first column resolve to the lowest row; the last two cases put 1500 / 1400
+    rows (three per thread) into one CTA."""
     rng = np.random.default_rng(m * 31 + w)
     W = rng.standard_normal((m, w)).astype(np.float32)
     W[rng.integers(0, m, 5), 0] = 3.0        # exact ties in the first column: lowest row wins
