@@ -215,3 +215,82 @@ def test_batch_independent():
     for (x, info), A, b in zip(res, As, bs):
         assert info.converged
         assert np.array_equal(x, solve(A, b, p)[0])
+
+
+def test_componentwise_berr_oettli_prager():
+    """The componentwise backward error (Table 2, middle column) is the smallest eps with
+    (A + dA) x = b + db, |dA| <= eps |A|, |db| <= eps |b| (Oettli-Prager): the perturbation
+    dA = D |A| diag(sign x), db = -D |b| with D = diag(r_i / (|A||x| + |b|)_i) attains it."""
+    from oracle.ir import componentwise_berr
+    rng = np.random.default_rng(21)
+    n = 40
+    A = rng.standard_normal((n, n))
+    x = rng.standard_normal(n)
+    b = A @ x + 1e-6 * rng.standard_normal(n)
+    r = b - A @ x
+    om = componentwise_berr(A, x, b, r)
+    den = np.abs(A) @ np.abs(x) + np.abs(b)
+    D = r / den
+    dA = D[:, None] * np.abs(A) * np.sign(x)[None, :]
+    db = -D * np.abs(b)
+    assert np.abs((A + dA) @ x - (b + db)).max() <= 1e-13 * den.max()
+    assert np.all(np.abs(dA) <= om * np.abs(A) * (1 + 1e-15))
+    assert np.all(np.abs(db) <= om * np.abs(b) * (1 + 1e-15))
+    # row i0 needs eps >= |r_i0| / den_i0 = om for any admissible perturbation
+    assert om == pytest.approx(np.abs(D).max(), rel=1e-15)
+    # normwise <= componentwise (|r_i| <= om (||A|| ||x|| + ||b||) for every row)
+    assert normwise_berr(A, x, b, r) <= om
+    # a diagonal system by hand: r = (0.5, 0, 0), |A||x| + |b| = (4.5, 6, 0), and 0/0 counts 0
+    Ad = np.diag([2.0, -3.0, 0.0])
+    xd = np.array([1.0, 1.0, 5.0])
+    bd = np.array([2.5, -3.0, 0.0])
+    assert componentwise_berr(Ad, xd, bd) == pytest.approx(0.5 / 4.5, rel=1e-15)
+    assert componentwise_berr(np.zeros((1, 1)), np.ones(1), np.zeros(1)) == 0.0
+
+
+def test_sir_error_recursion():
+    """Algorithm 1 with an LU solve: x_{i+1} = x_i + M^-1 (b - A x_i), so the error obeys
+    e_{i+1} = (I - M^-1 A) e_i up to rounding (M = the u_f factors, applied in FP64)."""
+    n = 30
+    A = randsvd(n, 1e2, seed=4)
+    xs = normal_vector(n, 5)
+    b = A @ xs
+    p = Params(uf="bf16", u="fp64", ur="dd", ua="fp64", imax=1, target=0.0, solver="sir")
+    F = lum.lu_block(A, "bf16", w=64)
+    x0 = lum.apply_minv(F, b, "fp64")
+    x1, info, _, _ = solve(A, b, p, F=F)
+    Minv = np.column_stack([lum.apply_minv(F, e, "fp64") for e in np.eye(n)])
+    G = np.eye(n) - Minv @ A
+    e0, e1 = x0 - xs, x1 - xs
+    assert np.linalg.norm(G @ e0 - e1) <= 1e-6 * np.linalg.norm(e0)
+    assert np.linalg.norm(e1) < 0.5 * np.linalg.norm(e0)
+    assert info.its == [0] and info.steps == 1
+
+
+def test_sir_condition_limit():
+    """SIR converges when kappa_inf(A) u_f < 1 and fails far above it, where GMRES-IR with
+    the same factors still converges (the constraint the paper sets against GMRES-IR)."""
+    n = 60
+    b = rhs_uniform(n, 3)
+    ok = randsvd(n, 10.0, seed=2)
+    assert np.linalg.cond(ok, np.inf) * UNIT_ROUNDOFF["bf16"] < 1
+    x, info, _, _ = solve(ok, b, Params(uf="bf16", u="fp64", ur="fp64", ua="fp64", imax=10, solver="sir"))
+    assert info.converged and info.berr[-1] <= 2 * UNIT_ROUNDOFF["fp64"]
+    hard = randsvd(n, 1e6, seed=2)
+    x, info, _, _ = solve(hard, b, Params(uf="bf16", u="fp64", ur="fp64", ua="fp64", imax=10, solver="sir"))
+    assert not info.converged and info.status in ("NOT_CONVERGED", "NONFINITE")
+    x, info, _, _ = solve(hard, b, Params(uf="bf16", u="fp64", ur="fp64", ua="fp64", m=n, k=0, imax=10))
+    assert info.converged
+
+
+def test_stop_componentwise():
+    """stop='cw' ends only when both the normwise and the componentwise backward errors meet
+    the target; omega_i >= eta_i at every step."""
+    A = randsvd(80, 1e4, seed=6)
+    b = rhs_uniform(80, 6)
+    p = Params(uf="bf16", u="fp64", ur="dd", ua="fp64", m=20, k=5, imax=10, stop="cw")
+    x, info, _, _ = solve(A, b, p)
+    assert info.converged
+    assert info.cberr[-1] <= 2 * UNIT_ROUNDOFF["fp64"] and info.berr[-1] <= 2 * UNIT_ROUNDOFF["fp64"]
+    assert all(c >= e for c, e in zip(info.cberr, info.berr))
+    assert len(info.cberr) == len(info.berr) == info.steps + 1
