@@ -74,6 +74,15 @@ typedef struct {
 /* gir_batch_solve: measure (gir_autotune) the size classes of the batch that have no tuned
  * values yet before solving. */
 #define GIR_FLAG_AUTOTUNE 0x1u
+/* Also compute the componentwise backward error omega_i = max_j |r_j| / (|A||x_i| + |b|)_j of
+ * every iterate (Table 2, middle column; fused into the residual pass, which then does one more
+ * FP64 multiply-add per matrix entry) and stop only when eta_i and omega_i both meet
+ * target_berr. Forward solves only: gir_solve_adjoint reports omega_i = -1. */
+#define GIR_FLAG_CW_BERR 0x2u
+/* Comparator: general iterative refinement (Algorithm 1, SIR) with the correction d = U^-1 L^-1 r
+ * by substitution with the u_f factors (applied as M^-1 is for GCRO-DR), in place of GCRO-DR.
+ * m, k, tau and carry_mode are ignored; its[i] = 0. */
+#define GIR_FLAG_SIR 0x4u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64
@@ -91,6 +100,8 @@ typedef struct {
     int k_eff;                  /* recycle dimension at exit */
     float ms_factor;            /* device time of gir_factor (CUDA events) */
     float ms_solve;             /* device time of the refinement loop */
+    double cw_berr[GIR_MAX_IR + 1]; /* omega_i with GIR_FLAG_CW_BERR (forward solves), else -1 */
+    double final_cw_berr;
 } gir_info;
 
 typedef struct gir_handle gir_handle;
@@ -157,6 +168,15 @@ int64_t gir_handle_n(const gir_handle* h);
  * All device pointers; r must not alias x or b. */
 gir_status gir_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
                         double* r, gir_prec prec, void* stream);
+
+/* Backward errors of an approximate solution x (the stop test of Algorithm 4, line 7, and the
+ * two backward-error columns of Table 2): with r = b - A x in precision prec (GIR_FP64 or GIR_DD),
+ *   *eta   = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf)          (normwise)
+ *   *omega = max_i |r_i| / (|A| |x| + |b|)_i, with 0/0 = 0          (componentwise).
+ * A, x, b: device (A n x n row-major, lda >= n); eta, omega: host, either may be NULL.
+ * Allocates a small workspace; synchronises the stream. */
+gir_status gir_backward_errors(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
+                               gir_prec prec, double* eta, double* omega, void* stream);
 
 /* w = A v (trans = 0) or w = A^T v (trans = 1) in FP64 arithmetic (device pointers). */
 gir_status gir_gemv(const double* A, int64_t n, int64_t lda, const double* v, double* w,

@@ -26,7 +26,7 @@ constexpr int KMAX = SM_KMAX;
 constexpr int MMAX = SM_MMAX;
 
 // device scalar slots
-enum { SC_RINF = 0, SC_XINF, SC_BINF, SC_AINF, SC_NRM2, SC_ONE, SC_S, SC_COUNT = 16 };
+enum { SC_RINF = 0, SC_XINF, SC_BINF, SC_AINF, SC_NRM2, SC_ONE, SC_S, SC_OMEGA, SC_COUNT = 16 };
 
 struct Recycle {
     double* U = nullptr;  // n x KMAX
@@ -80,6 +80,7 @@ struct gir_handle {
     double* dsc = nullptr;   // device scalars
     int* dflags = nullptr;
     double* hsc = nullptr;   // pinned host mirror of dsc
+    float ms_factor = 0.f;   // device time of the factorization, reported in every gir_info
     SmallState* hst = nullptr;  // pinned host mirror of the SmallState header
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     LUPlan plan;
@@ -169,7 +170,7 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->k < 0 || p->k >= p->m || p->k > GIR_MAX_K) return GIR_INVALID_ARG;
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
-    if ((p->flags & ~GIR_FLAG_AUTOTUNE) != 0) return GIR_INVALID_ARG;
+    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR)) != 0) return GIR_INVALID_ARG;
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
     if (p->ur != GIR_FP64 && p->ur != GIR_DD) return GIR_UNSUPPORTED;
@@ -496,11 +497,15 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
     double target = h->p.target_berr;
     if (target < 0.0) target = 2.0 * unit_roundoff(h->p.u);
     loc.status = GIR_NOT_CONVERGED;
+    for (int i = 0; i <= GIR_MAX_IR; ++i) loc.cw_berr[i] = -1.0;
+    loc.final_cw_berr = -1.0;
+    const bool cw = (h->p.flags & GIR_FLAG_CW_BERR) && !trans;
+    const bool sir = (h->p.flags & GIR_FLAG_SIR) != 0;
     for (int i = 0; i <= imax; ++i) {
         // r_i = b - A x_i in u_r (line 4), stored in u
         { int tslot_ = trace_begin(s);
         if (!trans) {
-            GIR_TRY(launch_residual(A, n, lda, x, b, h->rr, h->p.ur == GIR_DD, s));
+            GIR_TRY(launch_residual(A, n, lda, x, b, h->rr, h->p.ur == GIR_DD, s, cw ? h->dsc + SC_OMEGA : nullptr));
         } else {
             GIR_TRY(launch_gemv(A, n, lda, x, h->vtmp, 1, h->scratch, s));
             count_launch(), k_sub<<<grid1(n), 256, 0, s>>>(b, h->vtmp, h->rr, n);
@@ -515,23 +520,31 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
         const double eta = rinf / (nA * xinf + binf);
         loc.berr[i] = eta;
         loc.final_berr = eta;
+        const double omega = cw ? h->hsc[SC_OMEGA] : -1.0;
+        loc.cw_berr[i] = omega;
+        loc.final_cw_berr = omega;
         if (!(eta == eta) || !(xinf <= 1.7976931348623157e308)) {
             loc.status = GIR_NONFINITE;
             break;
         }
-        if (eta <= target) {
+        if (eta <= target && (!cw || omega <= target)) {
             loc.status = GIR_OK;
             break;
         }
         if (i == imax) break;
         // r^ = fl_u(r / ||r||_inf) ; c = M^-1 r^ (line 5 right-hand side)
         GIR_TRY(launch_scale_by(h->rr, n, h->dsc + SC_RINF, 1, r32, s));
-        GIR_TRY(apply_minv_h(h, h->rr, h->cvec, trans, s));
         int its = 0, capp = 0, conv = 0;
-        gir_status gs = gcrodr(h, A, lda, trans, rc, h->cvec, h->dvec, &its, &capp, &loc.cycles, &conv, s);
-        if (gs != GIR_OK) {
-            loc.status = gs;
-            break;
+        if (sir) {
+            // Algorithm 1, line 5: the correction by substitution with the factors, d = M^-1 r^
+            GIR_TRY(apply_minv_h(h, h->rr, h->dvec, trans, s));
+        } else {
+            GIR_TRY(apply_minv_h(h, h->rr, h->cvec, trans, s));
+            gir_status gs = gcrodr(h, A, lda, trans, rc, h->cvec, h->dvec, &its, &capp, &loc.cycles, &conv, s);
+            if (gs != GIR_OK) {
+                loc.status = gs;
+                break;
+            }
         }
         loc.its[i] = its;
         loc.carry_applies[i] = capp;
@@ -753,7 +766,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
         free_handle(h);
         return st;
     }
-    h->hsc[SC_COUNT - 2] = ms;
+    h->ms_factor = ms;
     *out = h;
     return GIR_OK;
 }
@@ -761,7 +774,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
 gir_status gir_solve(gir_handle* h, const double* A, int64_t lda, const double* b, double* x, gir_info* info,
                      void* stream) {
     if (!h || !A || !b || !x || lda < h->n) return GIR_INVALID_ARG;
-    if (info) info->ms_factor = (float)h->hsc[SC_COUNT - 2];
+    if (info) info->ms_factor = h->ms_factor;
     return refine(h, A, lda, b, x, info, 0, (cudaStream_t)stream);
 }
 
@@ -776,7 +789,7 @@ gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const 
         h->normAT = h->hsc[SC_AINF];
         h->normAT_ptr = A;
     }
-    if (info) info->ms_factor = (float)h->hsc[SC_COUNT - 2];
+    if (info) info->ms_factor = h->ms_factor;
     return refine(h, A, lda, g, lambda, info, 1, s);
 }
 
@@ -787,6 +800,32 @@ gir_status gir_residual(const double* A, int64_t n, int64_t lda, const double* x
     cudaStream_t s = (cudaStream_t)stream;
     GIR_TRY(launch_residual(A, n, lda, x, b, r, prec == GIR_DD, s));
     GIR_CUDA_TRY(cudaStreamSynchronize(s));
+    return GIR_OK;
+}
+
+gir_status gir_backward_errors(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
+                               gir_prec prec, double* eta, double* omega, void* stream) {
+    if (!A || !x || !b || n < 1 || lda < n) return GIR_INVALID_ARG;
+    if (prec != GIR_FP64 && prec != GIR_DD) return GIR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    // workspace: r (n) | row sums of |A| (n) | ||A||, ||x||, ||b||, ||r||, omega
+    double* w = nullptr;
+    GIR_TRY(dalloc_t(&w, (size_t)2 * n + 5));
+    double* r = w;
+    double* sc = w + 2 * n;
+    gir_status st = launch_residual(A, n, lda, x, b, r, prec == GIR_DD, s, sc + 4);
+    if (st == GIR_OK) st = launch_matrix_norminf(A, n, lda, sc + 0, w + n, s);
+    if (st == GIR_OK) st = launch_norminf(x, n, sc + 1, s);
+    if (st == GIR_OK) st = launch_norminf(b, n, sc + 2, s);
+    if (st == GIR_OK) st = launch_norminf(r, n, sc + 3, s);
+    double hs[5] = {0, 0, 0, 0, 0};
+    if (st == GIR_OK && cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = GIR_CUDA_ERROR;
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == GIR_OK) st = GIR_CUDA_ERROR;
+    cudaFree(w);
+    if (st != GIR_OK) return st;
+    if (eta) eta[0] = hs[3] / (hs[0] * hs[1] + hs[2]);
+    if (omega) omega[0] = hs[4];
     return GIR_OK;
 }
 

@@ -132,8 +132,10 @@ __device__ __forceinline__ uint16_t float_to_uf(float x, int fmt) {
 
 // ----------------------------------------------------------------------------- launchers
 // vector / tall-skinny kernels (k_vec.cu)
+// r = b - A x in FP64 (dd = 0) or double-double (dd = 1); with omega != nullptr also the
+// componentwise backward error max_i |r_i| / (|A||x| + |b|)_i into the device scalar *omega
 gir_status launch_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
-                           double* r, int dd, cudaStream_t s);
+                           double* r, int dd, cudaStream_t s, double* omega = nullptr);
 gir_status launch_gemv(const double* A, int64_t n, int64_t lda, const double* v, double* w,
                        int trans, double* scratch, cudaStream_t s);
 // out[c] = sum_i X[i, c] * y[i] for c < ncols (X column-major, stride ldx); partial sums in scratch

@@ -13,15 +13,19 @@ namespace gir {
 // MODE 1: r_i = b_i - sum_j a_ij x_j      (FP64 FMA)
 // MODE 2: r_i = b_i - sum_j a_ij x_j      (double-double: exact FMA products, TwoSum accumulation)
 // One warp per row, 16-byte loads along the row when the row start is 16-byte aligned.
-template <int MODE, bool VEC>
+// CW (MODE 1, 2): also den_i = sum_j |a_ij| |x_j| + |b_i| and the componentwise backward error
+// omega = max_i |r_i| / den_i (0/0 = 0, r/0 = inf), merged into *omax as the bit pattern of a
+// non-negative double (those order like unsigned integers).
+template <int MODE, bool VEC, bool CW>
 __global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, int64_t n, int64_t lda,
                                                 const double* __restrict__ x, const double* __restrict__ b,
-                                                double* __restrict__ out) {
+                                                double* __restrict__ out, unsigned long long* __restrict__ omax) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double qmax = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps_total) {
         const double* row = A + i * lda;
-        double sh = 0.0, sl = 0.0;
+        double sh = 0.0, sl = 0.0, den = 0.0;
         if (VEC) {
             const double2* row2 = reinterpret_cast<const double2*>(row);
             const double2* x2 = reinterpret_cast<const double2*>(x);
@@ -30,6 +34,7 @@ __global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, in
             for (int64_t j = lane; j < n2; j += 32) {
                 double2 a = __ldcs(row2 + j);
                 double2 v = __ldg(x2 + j);
+                if (CW) den = fma(fabs(a.x), fabs(v.x), fma(fabs(a.y), fabs(v.y), den));
                 if (MODE == 2) {
                     double p = a.x * v.x, e = fma(a.x, v.x, -p);
                     double s = sh + p, bb = s - sh, t = (sh - (s - bb)) + (p - bb);
@@ -44,6 +49,7 @@ __global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, in
             }
             if ((n & 1) && lane == 0) {
                 double a = row[n - 1], v = x[n - 1];
+                if (CW) den = fma(fabs(a), fabs(v), den);
                 if (MODE == 2) {
                     double p = a * v, e = fma(a, v, -p);
                     double s = sh + p, bb = s - sh, t = (sh - (s - bb)) + (p - bb);
@@ -56,6 +62,7 @@ __global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, in
 #pragma unroll 4
             for (int64_t j = lane; j < n; j += 32) {
                 double a = __ldcs(row + j), v = __ldg(x + j);
+                if (CW) den = fma(fabs(a), fabs(v), den);
                 if (MODE == 2) {
                     double p = a * v, e = fma(a, v, -p);
                     double s = sh + p, bb = s - sh, t = (sh - (s - bb)) + (p - bb);
@@ -65,9 +72,13 @@ __global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, in
                 }
             }
         }
+        double ri = 0.0;
         if (MODE != 2) {
             double s = warp_sum(sh + sl);
-            if (lane == 0) out[i] = (MODE == 0) ? s : (b[i] - s);
+            if (lane == 0) {
+                ri = (MODE == 0) ? s : (b[i] - s);
+                out[i] = ri;
+            }
         } else {
             // double-double butterfly reduction of (sh, sl)
 #pragma unroll
@@ -84,8 +95,29 @@ __global__ void __launch_bounds__(256) k_rowdot(const double* __restrict__ A, in
                 double bi = b[i];
                 double s = bi - sh, bb = s - bi, t = (bi - (s - bb)) + (-sh - bb);
                 t -= sl;
-                out[i] = s + t;
+                ri = s + t;
+                out[i] = ri;
             }
+        }
+        if (CW) {
+            den = warp_sum(den);
+            if (lane == 0) {
+                const double d = den + fabs(b[i]);
+                const double q = (d > 0.0) ? fabs(ri) / d : (ri == 0.0 ? 0.0 : __longlong_as_double(0x7ff0000000000000ll));
+                // NaN compares false: keep it visible by taking its (largest) bit pattern
+                qmax = (q >= qmax || !(q == q)) ? q : qmax;
+            }
+        }
+    }
+    if (CW) {
+        __shared__ unsigned long long wmax[8];
+        const unsigned long long qb = (unsigned long long)__double_as_longlong(fabs(qmax));
+        if (lane == 0) wmax[threadIdx.x >> 5] = qb;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+            atomicMax(omax, m);
         }
     }
 }
@@ -102,17 +134,21 @@ static bool aligned16(const void* p, int64_t ld) {
 }
 
 gir_status launch_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
-                           double* r, int dd, cudaStream_t s) {
+                           double* r, int dd, cudaStream_t s, double* omega) {
     if (n <= 0) return GIR_OK;
     int g = grid_for_rows(n);
     bool v = aligned16(A, lda) && ((uintptr_t)x % 16 == 0);
+    unsigned long long* om = reinterpret_cast<unsigned long long*>(omega);
+    if (om) GIR_CUDA_TRY(cudaMemsetAsync(om, 0, sizeof(double), s));
+#define GIR_ROWDOT(M, V)                                                                      \
+    if (om) count_launch(), k_rowdot<M, V, true><<<g, 256, 0, s>>>(A, n, lda, x, b, r, om);  \
+    else count_launch(), k_rowdot<M, V, false><<<g, 256, 0, s>>>(A, n, lda, x, b, r, nullptr)
     if (dd) {
-        if (v) count_launch(), k_rowdot<2, true><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
-        else count_launch(), k_rowdot<2, false><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
+        if (v) { GIR_ROWDOT(2, true); } else { GIR_ROWDOT(2, false); }
     } else {
-        if (v) count_launch(), k_rowdot<1, true><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
-        else count_launch(), k_rowdot<1, false><<<g, 256, 0, s>>>(A, n, lda, x, b, r);
+        if (v) { GIR_ROWDOT(1, true); } else { GIR_ROWDOT(1, false); }
     }
+#undef GIR_ROWDOT
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
@@ -152,8 +188,8 @@ gir_status launch_gemv(const double* A, int64_t n, int64_t lda, const double* v,
     if (n <= 0) return GIR_OK;
     if (!trans) {
         int g = grid_for_rows(n);
-        if (aligned16(A, lda) && ((uintptr_t)v % 16 == 0)) count_launch(), k_rowdot<0, true><<<g, 256, 0, s>>>(A, n, lda, v, nullptr, w);
-        else count_launch(), k_rowdot<0, false><<<g, 256, 0, s>>>(A, n, lda, v, nullptr, w);
+        if (aligned16(A, lda) && ((uintptr_t)v % 16 == 0)) count_launch(), k_rowdot<0, true, false><<<g, 256, 0, s>>>(A, n, lda, v, nullptr, w, nullptr);
+        else count_launch(), k_rowdot<0, false, false><<<g, 256, 0, s>>>(A, n, lda, v, nullptr, w, nullptr);
     } else {
         dim3 grid((unsigned)((n + GT_COLS - 1) / GT_COLS), (unsigned)((n + GT_ROWS - 1) / GT_ROWS));
         count_launch(), k_gemv_t_partial<<<grid, 256, 0, s>>>(A, n, lda, v, scratch);

@@ -36,7 +36,7 @@ class CInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("ir_steps", C.c_int), ("total_its", C.c_int), ("its", C.c_int * GIR_MAX_IR),
                 ("carry_applies", C.c_int * GIR_MAX_IR), ("berr", C.c_double * (GIR_MAX_IR + 1)),
                 ("final_berr", C.c_double), ("cycles", C.c_int), ("k_eff", C.c_int), ("ms_factor", C.c_float),
-                ("ms_solve", C.c_float)]
+                ("ms_solve", C.c_float), ("cw_berr", C.c_double * (GIR_MAX_IR + 1)), ("final_cw_berr", C.c_double)]
 
 
 SYMBOLS = {
@@ -55,6 +55,8 @@ SYMBOLS = {
     "gir_handle_n": (C.c_int64, [C.c_void_p]),
     "gir_residual": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                C.c_void_p]),
+    "gir_backward_errors": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "gir_gemv": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "gir_export_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.POINTER(C.c_double), C.c_void_p]),
@@ -131,6 +133,8 @@ class Params:
 
 
 GIR_FLAG_AUTOTUNE = 0x1
+GIR_FLAG_CW_BERR = 0x2   # also compute the componentwise backward error and stop on both
+GIR_FLAG_SIR = 0x4       # Algorithm 1 comparator: correction by substitution, no GCRO-DR
 
 
 @dataclass
@@ -146,12 +150,16 @@ class Info:
     k_eff: int
     ms_factor: float
     ms_solve: float
+    cw_berr: list = field(default_factory=list)
+    final_cw_berr: float = -1.0
 
     @classmethod
     def from_c(cls, ci: CInfo):
         s = ci.ir_steps
-        return cls(ci.status, s, ci.total_its, list(ci.its[:s]), list(ci.carry_applies[:s]), list(ci.berr[:s + 1]),
-                   ci.final_berr, ci.cycles, ci.k_eff, ci.ms_factor, ci.ms_solve)
+        nb = s + 1
+        return cls(ci.status, s, ci.total_its, list(ci.its[:s]), list(ci.carry_applies[:s]), list(ci.berr[:nb]),
+                   ci.final_berr, ci.cycles, ci.k_eff, ci.ms_factor, ci.ms_solve, list(ci.cw_berr[:nb]),
+                   ci.final_cw_berr)
 
     @property
     def converged(self):
@@ -288,6 +296,17 @@ def residual(A, x, b, prec="fp64", stream=None):
     if st != GIR_OK:
         raise GirError(st, "gir_residual")
     return r
+
+
+def backward_errors(A, x, b, prec="fp64", stream=None):
+    """(eta, omega): normwise and componentwise backward errors of x (Table 2's two columns)."""
+    n, lda = _check_matrix(A)
+    eta, om = C.c_double(0.0), C.c_double(0.0)
+    st = load().gir_backward_errors(_ptr(A), n, lda, _ptr(x), _ptr(b), PREC[prec], C.byref(eta), C.byref(om),
+                                    _stream(stream))
+    if st != GIR_OK:
+        raise GirError(st, "gir_backward_errors")
+    return eta.value, om.value
 
 
 def gemv(A, v, trans=False, stream=None):

@@ -58,3 +58,25 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(gir, "_lib", None)
     with pytest.raises(RuntimeError):
         gir.load()
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof/offsetof of gir_params and gir_info from gcc on include/gir.h equal the ctypes mirrors."""
+    import shutil
+    import subprocess
+    from paper_2201_09827_gb300 import gir
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gir.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(gir_params), sizeof(gir_info),'
+                   ' offsetof(gir_info, ms_solve), offsetof(gir_info, cw_berr), offsetof(gir_info, final_cw_berr));'
+                   'return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(gir.CParams), ctypes.sizeof(gir.CInfo), gir.CInfo.ms_solve.offset,
+            gir.CInfo.cw_berr.offset, gir.CInfo.final_cw_berr.offset]
+    assert got == want

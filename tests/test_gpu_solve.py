@@ -39,20 +39,21 @@ def gpu_factors_for_oracle(F, n, uf):
                        R.cpu().numpy(), S.cpu().numpy(), mu)
 
 
-def run_both(pkg, A, b, uf, u, ur, m, k, tau, imax=10, target=None, max_its=None, carry=1, same_factors=False):
+def run_both(pkg, A, b, uf, u, ur, m, k, tau, imax=10, target=None, max_its=None, carry=1, same_factors=False,
+             flags=0, solver="gcrodr", stop="berr"):
     """GPU solve and oracle solve. same_factors=True gives the oracle the GPU's u_f factors, which
     isolates the refinement/GCRO-DR part for problems whose iteration counts are sensitive to the
     FP32 summation order of the factorization (poor preconditioners, kappa * u_f >> 1)."""
     prm = pkg.Params(uf=uf, u=u, ur=ur, m=m, k=k, tau=tau, imax=imax,
                      target_berr=-1.0 if target is None else target, carry_mode=carry,
-                     max_its=max_its or 0)
+                     max_its=max_its or 0, flags=flags)
     F = pkg.Factorization(cuda(A), prm)
     x, info = F.solve(cuda(A), cuda(b))
     x = x.cpu().numpy()
     Fo = gpu_factors_for_oracle(F, A.shape[0], uf) if same_factors else None
     F.close()
     op = OP(uf=uf, u=u, ur=ur, ua="u" if u == "fp64" else "u2", m=m, k=k, tau=tau, imax=imax, target=target,
-            lu_w=32, max_its=max_its or 20 * m, carry_mode=carry)
+            lu_w=32, max_its=max_its or 20 * m, carry_mode=carry, solver=solver, stop=stop)
     xo, io, _, _ = osolve(A, b, op, F=Fo)
     return x, info, xo, io
 
@@ -353,3 +354,86 @@ def test_fp8_solve_parity(pkg, n, kappa, m):
     x, info, xo, io = run_both(pkg, A, b, "e4m3", "fp64", "fp64", m, 10, 1e-8, target=1e-15)
     assert_parity(A, b, x, info, xo, io, "fp64")
     assert normwise_berr(A, x, b) <= 1e-15
+
+
+@pytest.mark.parametrize("n,pad", [(1000, 0), (1003, 5)])
+def test_backward_errors_parity(pkg, n, pad):
+    """gir_backward_errors against the oracle's normwise and componentwise definitions, with an
+    odd n, a padded leading dimension and a zero row with b_i = 0 (0/0 counts 0)."""
+    from oracle.ir import componentwise_berr, residual as oresidual
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A[7, :] = 0.0
+    xs = rng.standard_normal(n)
+    x = xs + 1e-6 * rng.standard_normal(n)
+    b = A @ xs
+    b[7] = 0.0
+    Ap = np.zeros((n, n + pad))
+    Ap[:, :n] = A
+    Ad = cuda(Ap)[:, :n]
+    xd, bd = cuda(x), cuda(b)
+    r = oresidual(A, x, b, "dd")
+    eta_o, om_o = normwise_berr(A, x, b, r), componentwise_berr(A, x, b, r)
+    # FP64 residual: |r| ~ 1e-6 sqrt(n) against rounding ~ sqrt(n) u |A||x|, so ~1e-7 relative
+    for prec, tol in (("fp64", 1e-5), ("dd", 1e-12)):
+        eta, om = pkg.backward_errors(Ad, xd, bd, prec)
+        assert eta == pytest.approx(eta_o, rel=tol) and om == pytest.approx(om_o, rel=tol)
+        assert eta <= om
+    # x = 0, b = 0: every row is 0/0
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    assert pkg.backward_errors(Ad, z, z, "dd")[1] == 0.0
+
+
+@pytest.mark.parametrize("kappa,uf", [(1e1, "fp16"), (1e2, "fp16")])
+def test_sir_comparator_parity(pkg, kappa, uf):
+    """GIR_FLAG_SIR (Algorithm 1, correction by substitution) against the oracle's SIR on the same
+    u_f factors: the same status, the same number of steps and the same backward errors per step
+    (the iteration is linear, e_{i+1} = (I - M^-1 A) e_i, so rounding differences stay relative)."""
+    from paper_2201_09827_gb300 import gir
+    n = 768
+    A = randsvd(n, kappa, seed=3)
+    b = A @ normal_vector(n, 4)
+    x, info, xo, io = run_both(pkg, A, b, uf, "fp64", "fp64", 30, 0, 1e-8, imax=12, target=1e-15,
+                               same_factors=True, flags=gir.GIR_FLAG_SIR, solver="sir")
+    assert io.converged and info.status == gir.GIR_OK
+    assert info.ir_steps == io.steps and info.its == [0] * info.ir_steps
+    for e, eo in zip(info.berr, io.berr):
+        if eo > 1e-13:
+            assert e == pytest.approx(eo, rel=1e-3)
+    assert normwise_berr(A, x, b) <= 1e-15
+
+
+def test_sir_fails_where_gmres_ir_converges(pkg):
+    """kappa_inf u_f >> 1: SIR does not converge (reported, not hidden) while RGMRES-IR with the same
+    factorization does, as in the oracle."""
+    from paper_2201_09827_gb300 import gir
+    n = 512
+    A = randsvd(n, 1e6, seed=5)
+    b = rhs_uniform(n, 5)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 30, 0, 1e-8, imax=8, target=1e-15,
+                               same_factors=True, flags=gir.GIR_FLAG_SIR, solver="sir")
+    assert not io.converged and info.status in (gir.GIR_NOT_CONVERGED, gir.GIR_NONFINITE)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 50, 10, 1e-8, imax=8, target=1e-15)
+    assert info.status == gir.GIR_OK and io.converged
+
+
+def test_componentwise_stop_parity(pkg):
+    """GIR_FLAG_CW_BERR: omega_i per step against the oracle's stop='cw' run on the same factors;
+    omega_i >= eta_i; the run ends with both <= 2u; the final omega equals gir_backward_errors."""
+    from paper_2201_09827_gb300 import gir
+    n = 1024
+    A = randsvd(n, 1e4, seed=8)
+    b = rhs_uniform(n, 8)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 40, 8, 1e-8, target=2 * UNIT_ROUNDOFF["fp64"],
+                               same_factors=True, flags=gir.GIR_FLAG_CW_BERR, stop="cw")
+    assert info.status == gir.GIR_OK and io.converged
+    assert len(info.cw_berr) == info.ir_steps + 1
+    assert info.final_cw_berr <= 2 * UNIT_ROUNDOFF["fp64"] and info.final_berr <= 2 * UNIT_ROUNDOFF["fp64"]
+    assert all(c >= e * (1 - 1e-12) for c, e in zip(info.cw_berr, info.berr))
+    assert info.cw_berr[0] == pytest.approx(io.cberr[0], rel=1e-6)
+    assert abs(info.ir_steps - io.steps) <= 1
+    eta, om = pkg.backward_errors(cuda(A), cuda(x), cuda(b), "fp64")
+    assert om == info.final_cw_berr and eta == pytest.approx(info.final_berr, rel=1e-12)
+    # without the flag omega is not computed
+    x2, info2, _, _ = run_both(pkg, A, b, "bf16", "fp64", "fp64", 40, 8, 1e-8, imax=0)
+    assert info2.cw_berr == [-1.0] * (info2.ir_steps + 1)
