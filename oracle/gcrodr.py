@@ -56,6 +56,7 @@ class GcroInfo:
     cycles: int = 0
     converged: bool = False
     k_eff: int = 0
+    k_used: int = 0           # recycle dimension used (differs from the argument with k_auto)
     resid: list = field(default_factory=list)   # Givens residual estimate after each Arnoldi step
 
 
@@ -184,7 +185,7 @@ def _lstsq(G, rhs):
     return sla.solve_triangular(R, Q.T @ rhs, lower=False)
 
 
-def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None):
+def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_auto=None):
     """Solve A~ d = c by GCRO-DR(m, k) from d0 = 0.
 
     op:     v -> A~ v (already rounded to u).
@@ -192,7 +193,10 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None):
     carry:  optional (U, C) pair with A~ U = C from the previous system; when given it is
             used instead of recomputing QR(A~ Y~) (same result in exact arithmetic,
             because A~ does not change between refinement steps).
-    Returns d, U (the Y~ for the next system), C, info.
+    k_auto: None, or a cap k_max: when the first (GMRES) cycle converges after j steps, the
+            recycle dimension becomes min(j - 1, k_max) -- Section 5's observation that recycling
+            the whole first-step subspace, k = its_1 - 1, gives the fewest iterations.
+    Returns d, U (the Y~ for the next system), C, info (info.k_used: the k that was used).
     """
     fu = (lambda z: round_to(z, u))
     c = np.asarray(c, dtype=np.float64)
@@ -227,6 +231,8 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None):
         info.its += j
         info.cycles += 1
         info.resid += est
+        if k_auto is not None and est and est[-1] <= tol:
+            k = min(j - 1, k_auto)
         beta = np.linalg.norm(r)
         rhs = np.zeros(j + 1)
         rhs[0] = beta
@@ -281,4 +287,5 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None):
                 U = fu(sla.solve_triangular(R, (Vhat @ P)[:, keep].T, trans="T", lower=False).T)
     info.converged = bool(np.linalg.norm(r) <= tol)
     info.k_eff = U.shape[1]
+    info.k_used = k
     return d, U, C, info

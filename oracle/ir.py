@@ -21,6 +21,9 @@ Readings (listed in DESIGN.md):
   u = FP64, Algorithm 4); 'u' means uniform precision (Section 4.3.1).
 * x0: in the paper's every-operation-rounded mode the substitution is in u_f; for the
   block-FMA factorization it is done in FP64 and rounded to u.
+* ``k_mode='knee'``: Section 5 reports the fewest total iterations for k = its_1 - 1, with its_1
+  the first step's count (the whole first-step subspace recycled). The first GCRO-DR call
+  fixes k this way when its first cycle converges; otherwise k stays as given.
 * Recycle carry between refinement steps: ``carry_mode=0`` recomputes QR(A~ Y~)
   literally; ``carry_mode=1`` reuses (U_k, C_k), valid because A~ U_k = C_k and A~ does
   not change between steps.
@@ -52,6 +55,8 @@ class Params:
     target: float | None = None   # normwise backward error target (default 2u)
     stop: str = "berr"            # 'berr', 'cw' (normwise and componentwise) or 'all'
     solver: str = "gcrodr"        # correction solver: 'gcrodr' (Algorithm 4) or 'sir' (Algorithm 1)
+    k_mode: str = "fixed"         # 'fixed', or 'knee': k = its_1 - 1 (capped at k_max), Section 5
+    k_max: int = 64
     carry_mode: int = 0
     lu_mode: str = "block"        # 'block' or 'chop'
     lu_w: int = 64
@@ -68,6 +73,7 @@ class IrInfo:
     converged: bool = False
     steps: int = 0
     k_eff: list = field(default_factory=list)
+    k_used: list = field(default_factory=list)     # recycle dimension per refinement step
     resid: list = field(default_factory=list)
     status: str = "NOT_CONVERGED"
 
@@ -159,6 +165,7 @@ def solve(A, b, p: Params, F=None, xstar=None, transpose=False, Y0=None):
     info = IrInfo()
     Y = Y0
     carry = None
+    kk = None          # the recycle dimension once k_mode='knee' has fixed it
     for i in range(p.imax + 1):
         r_ur = residual(Aop, x, b, p.ur)
         r = fu(r_ur)
@@ -195,12 +202,17 @@ def solve(A, b, p: Params, F=None, xstar=None, transpose=False, Y0=None):
         s = float(np.max(np.abs(r)))
         rhat = fu(r / s)
         c = minv(rhat)
-        d, U, C, gi = gcrodr(op, c, p.m, p.k, p.tau, Ytil=Y, u=p.u, max_its=p.max_its, carry=carry)
+        auto = p.k_max if (p.k_mode == "knee" and kk is None) else None
+        d, U, C, gi = gcrodr(op, c, p.m, p.k if kk is None else kk, p.tau, Ytil=Y, u=p.u, max_its=p.max_its,
+                             carry=carry, k_auto=auto)
+        if kk is None and p.k_mode == "knee":
+            kk = gi.k_used
+        info.k_used.append(gi.k_used)
         info.its.append(gi.its)
         info.carry_applies.append(gi.carry_applies)
         info.k_eff.append(gi.k_eff)
         info.resid.append(gi.resid)
-        if p.k > 0 and U.shape[1] > 0:
+        if (p.k if kk is None else kk) > 0 and U.shape[1] > 0:
             Y = U
             carry = (U, C) if p.carry_mode == 1 else None
         x = fu(x + s * d)

@@ -294,3 +294,24 @@ def test_stop_componentwise():
     assert info.cberr[-1] <= 2 * UNIT_ROUNDOFF["fp64"] and info.berr[-1] <= 2 * UNIT_ROUNDOFF["fp64"]
     assert all(c >= e for c, e in zip(info.cberr, info.berr))
     assert len(info.cberr) == len(info.berr) == info.steps + 1
+
+
+def test_knee_k_gives_fewest_iterations():
+    """Section 5 (Fig. 2): recycling the whole first-step subspace, k = its_1 - 1, gives the
+    fewest total GMRES iterations. k_mode='knee' picks that k from the first step and then equals
+    the fixed-k run with the same k."""
+    A = randsvd(200, 1e4, seed=0)
+    b = rhs_uniform(200, 0)
+    base = dict(uf="bf16", u="fp64", ur="fp64", ua="u", m=100, tau=1e-8, imax=10, lu_w=32)
+    xk, ik, _, _ = solve(A, b, Params(k=0, k_mode="knee", **base))
+    assert ik.converged and len(ik.its) >= 2
+    its1 = ik.its[0]
+    assert ik.k_used == [its1 - 1] * len(ik.its)
+    for k in (0, 5, 10, 20):
+        _, i, _, _ = solve(A, b, Params(k=k, **base))
+        assert i.its[0] == its1 and ik.total < i.total, (k, i.its, ik.its)
+    xf, i_f, _, _ = solve(A, b, Params(k=its1 - 1, **base))
+    assert i_f.its == ik.its and np.array_equal(xf, xk)
+    # the cap: k never exceeds k_max
+    _, ic, _, _ = solve(A, b, Params(k=0, k_mode="knee", k_max=7, **base))
+    assert ic.k_used[0] == 7
