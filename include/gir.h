@@ -83,6 +83,11 @@ typedef struct {
  * by substitution with the u_f factors (applied as M^-1 is for GCRO-DR), in place of GCRO-DR.
  * m, k, tau and carry_mode are ignored; its[i] = 0. */
 #define GIR_FLAG_SIR 0x4u
+/* Recycle dimension from the first refinement step (Section 5): when the first GMRES cycle of
+ * the handle's first GCRO-DR call converges after its_1 steps, k becomes min(its_1 - 1,
+ * GIR_MAX_K) -- the whole first-step subspace is recycled -- for that cycle's extraction and every
+ * later step and solve. If that cycle does not converge, params.k stays. info.k_eff reports it. */
+#define GIR_FLAG_ADAPTIVE_K 0x8u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64

@@ -81,6 +81,8 @@ struct gir_handle {
     int* dflags = nullptr;
     double* hsc = nullptr;   // pinned host mirror of dsc
     float ms_factor = 0.f;   // device time of the factorization, reported in every gir_info
+    int k_run = 0;           // recycle dimension in use (params k, or its_1 - 1 with GIR_FLAG_ADAPTIVE_K)
+    bool k_open = false;     // GIR_FLAG_ADAPTIVE_K: k is fixed by the next first GMRES cycle
     SmallState* hst = nullptr;  // pinned host mirror of the SmallState header
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     LUPlan plan;
@@ -170,7 +172,8 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->k < 0 || p->k >= p->m || p->k > GIR_MAX_K) return GIR_INVALID_ARG;
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
-    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR)) != 0) return GIR_INVALID_ARG;
+    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR | GIR_FLAG_ADAPTIVE_K)) != 0)
+        return GIR_INVALID_ARG;
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
     if (p->ur != GIR_FP64 && p->ur != GIR_DD) return GIR_UNSUPPORTED;
@@ -202,6 +205,10 @@ __global__ void k_axpy_dev(double* __restrict__ x, const double* __restrict__ d,
 __global__ void k_sub(const double* __restrict__ b, const double* __restrict__ t, double* __restrict__ r, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         r[i] = b[i] - t[i];
+}
+// The recycle dimension of the next cycle close (set once the first cycle's length is known).
+__global__ void k_set_ktarget(SmallState* st, int k) {
+    if (threadIdx.x == 0) st->k_target = k;
 }
 // Initialise the small state for a new cycle: beta from device memory, tol, counters.
 __global__ void k_cycle_init(SmallState* st, const double* beta, double tol, int kc, int first, int k, int m) {
@@ -313,7 +320,7 @@ gir_status run_cycle(gir_handle* h, const double* A, int64_t lda, int trans, int
     // v_1 = r / ||r||  (||r|| is in dsc[SC_NRM2])
     GIR_CUDA_TRY(cudaMemcpyAsync(V(h, 0), h->r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     GIR_TRY(launch_scale_by(V(h, 0), h->n, h->dsc + SC_NRM2, 1, h->round32, s));
-    count_launch(), k_cycle_init<<<1, 32, 0, s>>>(h->st, h->dsc + SC_NRM2, tol, kc, first, h->p.k, h->p.m);
+    count_launch(), k_cycle_init<<<1, 32, 0, s>>>(h->st, h->dsc + SC_NRM2, tol, kc, first, h->k_run, h->p.m);
     int j = 0;
     for (; j < steps; ++j) {
         GIR_TRY(arnoldi_step(h, A, lda, trans, j, kc, s));
@@ -331,7 +338,8 @@ gir_status run_cycle(gir_handle* h, const double* A, int64_t lda, int trans, int
 gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycle& rc, const double* c, double* d,
                   int* its_out, int* carry_applies, int* cycles, int* converged, cudaStream_t s) {
     const int64_t n = h->n;
-    const int m = h->p.m, k = h->p.k;
+    const int m = h->p.m;
+    int k = h->k_run;
     const int max_its = h->p.max_its > 0 ? h->p.max_its : 20 * m;
     const int r32 = h->round32;
     int its = 0;
@@ -391,6 +399,15 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
         its += j;
         ++ncyc;
         if (h->hst->status) return flags_status(h->hst->status | read_flags(h, s));
+        if (h->k_open) {
+            // Section 5: the fewest iterations came from recycling the whole first-step subspace,
+            // k = its_1 - 1; it applies when the first GMRES cycle converged
+            h->k_open = false;
+            if (h->hst->converged && j >= 1) {
+                h->k_run = k = min(j - 1, KMAX);
+                count_launch(), k_set_ktarget<<<1, 32, 0, s>>>(h->st, k);
+            }
+        }
         { int tslot_ = trace_begin(s);
         GIR_TRY(launch_cycle_close(h->st, h->qh, s));
         trace_end(tslot_, "cycle close", s); }
@@ -474,7 +491,7 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
     memset(&loc, 0, sizeof(loc));
     const int r32 = h->round32;
     Recycle& rc = trans ? h->adj : h->fwd;
-    if (trans && h->adj.k == 0 && h->fwd.k > 0 && h->p.k > 0) {
+    if (trans && h->adj.k == 0 && h->fwd.k > 0 && h->k_run > 0) {
         // seed the adjoint recycle space with the forward U_k (any Y~ is a valid start, Algorithm 3 line 2)
         h->adj.k = h->fwd.k;
         GIR_CUDA_TRY(cudaMemcpyAsync(h->adj.U, h->fwd.U, (size_t)h->fwd.k * n * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -625,6 +642,8 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     if (!h) return GIR_OOM;
     h->n = n;
     h->p = *params;
+    h->k_run = params->k;
+    h->k_open = (params->flags & GIR_FLAG_ADAPTIVE_K) != 0;
     h->fmt = (params->uf == GIR_FP16) ? FF_FP16 : FF_BF16;
     h->round32 = (params->u == GIR_FP32);
     h->scaled = (params->uf == GIR_FP16);

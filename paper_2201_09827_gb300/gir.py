@@ -135,6 +135,7 @@ class Params:
 GIR_FLAG_AUTOTUNE = 0x1
 GIR_FLAG_CW_BERR = 0x2   # also compute the componentwise backward error and stop on both
 GIR_FLAG_SIR = 0x4       # Algorithm 1 comparator: correction by substitution, no GCRO-DR
+GIR_FLAG_ADAPTIVE_K = 0x8  # k = its_1 - 1 from the first refinement step (Section 5)
 
 
 @dataclass
