@@ -55,8 +55,11 @@ typedef struct {
     gir_prec uf;        /* factorization precision u_f: GIR_FP16 (scaled), GIR_BF16, GIR_FP8_E4M3 */
     gir_prec u;         /* working precision u (storage of x, d, Krylov vectors): GIR_FP64 or GIR_FP32 */
     gir_prec ur;        /* residual precision u_r: GIR_FP64 or GIR_DD */
-    gir_prec ua;        /* precision of the A~ = M^-1 A application: GIR_FP64 (Section 4.3.1 uniform
-                           precision when u = FP64, u^2 when u = FP32) */
+    gir_prec ua;        /* precision of the A~ = M^-1 A application: GIR_FP64 (float-float A v and
+                           substitutions, about 2^-46: Section 4.3.1's uniform-precision reading
+                           for u = FP64, u^2 for u = FP32) or GIR_DD (double-double product and
+                           substitutions, about 2^-106: Algorithm 4's u^2 for u = FP64; ALU-bound
+                           on GB300's FP64 units and several times slower) */
     int m;              /* GCRO-DR restart length (maximum subspace size), 1 <= m <= GIR_MAX_M */
     int k;              /* recycle dimension, 0 <= k < m; k = 0 gives GMRES-IR(m) */
     double tau;         /* inner tolerance on the relative preconditioned residual */

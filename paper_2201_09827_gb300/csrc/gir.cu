@@ -16,6 +16,7 @@
 #include "k_lu.cuh"
 #include "k_small.cuh"
 #include "k_trsv.cuh"
+#include "k_dd.cuh"
 #include "trace.cuh"
 
 using namespace gir;
@@ -81,6 +82,8 @@ struct gir_handle {
     int* dflags = nullptr;
     double* hsc = nullptr;   // pinned host mirror of dsc
     float ms_factor = 0.f;   // device time of the factorization, reported in every gir_info
+    bool dd = false;         // u_a = double-double (the paper's u^2 for u = FP64)
+    DdState ddst;            // buffers of the double-double operator
     int k_run = 0;           // recycle dimension in use (params k, or its_1 - 1 with GIR_FLAG_ADAPTIVE_K)
     bool k_open = false;     // GIR_FLAG_ADAPTIVE_K: k is fixed by the next first GMRES cycle
     SmallState* hst = nullptr;  // pinned host mirror of the SmallState header
@@ -141,7 +144,9 @@ void free_handle_on(gir_handle* h, cudaStream_t s) {
     void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.perm, h->trsv.z, h->trsv.y1,
                     h->trsv.y2, h->trsv.ready, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
-                    h->scratch, h->st, h->qh, h->dsc, h->dflags, h->Ahi, h->Alo, h->vsplit};
+                    h->scratch, h->st, h->qh, h->dsc, h->dflags, h->Ahi, h->Alo, h->vsplit,
+                    h->ddst.DL, h->ddst.DU, h->ddst.z, h->ddst.y1, h->ddst.y2, h->ddst.w, h->ddst.part,
+                    h->ddst.ready};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     if (h->hsc) cudaFreeHost(h->hsc);
@@ -177,7 +182,7 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
     if (p->ur != GIR_FP64 && p->ur != GIR_DD) return GIR_UNSUPPORTED;
-    if (p->ua != GIR_FP64) return GIR_UNSUPPORTED;
+    if (p->ua != GIR_FP64 && p->ua != GIR_DD) return GIR_UNSUPPORTED;
     if (p->carry_mode != 0 && p->carry_mode != 1) return GIR_INVALID_ARG;
     return GIR_OK;
 }
@@ -271,22 +276,34 @@ gir_status flags_status(int f) {
 // w = M^-1 A v (trans: M^-T A^T v), rounded to u
 // A v for the correction equation: float-float from the split of A for A~ = M^-1 A (the triangular
 // solves are float-float too); FP64 for the transposed operator of the adjoint solve
+// The product of A~ = M^-1 A: float-float (A_hi + A_lo) v, FP64 A^T v, or with u_a = dd the
+// double-double product kept unrounded in ddst.w for the substitutions (w is then unused).
 gir_status launch_op_gemv(gir_handle* h, const double* A, int64_t lda, const double* v, double* w, int trans,
                           cudaStream_t s) {
+    if (h->dd) return gemv_dd(h->ddst, A, h->n, lda, v, trans, s);
     if (!trans) return launch_gemv_ff(h->Ahi, h->Alo, h->ldf, h->n, v, w, h->vsplit, s);
     return launch_gemv(A, h->n, lda, v, w, trans, h->scratch, s);
+}
+
+// M^-1 (or M^-T) applied to the output of launch_op_gemv
+gir_status apply_minv_op(gir_handle* h, double* w, int trans, cudaStream_t s) {
+    const double* R = h->scaled ? h->R : nullptr;
+    const double* S = h->scaled ? h->S : nullptr;
+    if (h->dd) return apply_minv_dd(h->ddst, h->trsv, nullptr, w, R, S, h->mu, trans, h->round32, h->dflags, s);
+    return apply_minv(h->trsv, h->vtmp, w, R, S, h->mu, trans, h->round32, h->dflags, s);
 }
 
 gir_status apply_atilde(gir_handle* h, const double* A, int64_t lda, const double* v, double* w, int trans,
                         cudaStream_t s) {
     GIR_TRY(launch_op_gemv(h, A, lda, v, h->vtmp, trans, s));
-    return apply_minv(h->trsv, h->vtmp, w, h->scaled ? h->R : nullptr, h->scaled ? h->S : nullptr, h->mu, trans,
-                      h->round32, h->dflags, s);
+    return apply_minv_op(h, w, trans, s);
 }
 
 gir_status apply_minv_h(gir_handle* h, const double* v, double* w, int trans, cudaStream_t s) {
-    return apply_minv(h->trsv, v, w, h->scaled ? h->R : nullptr, h->scaled ? h->S : nullptr, h->mu, trans, h->round32,
-                      h->dflags, s);
+    const double* R = h->scaled ? h->R : nullptr;
+    const double* S = h->scaled ? h->S : nullptr;
+    if (h->dd) return apply_minv_dd(h->ddst, h->trsv, v, w, R, S, h->mu, trans, h->round32, h->dflags, s);
+    return apply_minv(h->trsv, v, w, R, S, h->mu, trans, h->round32, h->dflags, s);
 }
 
 // One Arnoldi step j of (I - C C^T) A~ with CGS2 (Algorithm 3, line 15; first cycle line 7).
@@ -298,7 +315,7 @@ gir_status arnoldi_step(gir_handle* h, const double* A, int64_t lda, int trans, 
     GIR_TRY(launch_op_gemv(h, A, lda, vj, h->vtmp, trans, s));
     trace_end(tslot_, "gemv", s); }
     { int tslot_ = trace_begin(s);
-    GIR_TRY(apply_minv_h(h, h->vtmp, w, trans, s));
+    GIR_TRY(apply_minv_op(h, w, trans, s));
     trace_end(tslot_, "minv", s); }
     { int tslot_ = trace_begin(s);
     double* basis = Cregion(h, kc);
@@ -647,6 +664,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     h->fmt = (params->uf == GIR_FP16) ? FF_FP16 : FF_BF16;
     h->round32 = (params->u == GIR_FP32);
     h->scaled = (params->uf == GIR_FP16);
+    h->dd = (params->ua == GIR_DD);
     cudaGetDevice(&h->dev);
     gir_status st = GIR_OK;
 #define ALLOC(ptr, cnt)                                                             \
@@ -681,9 +699,23 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     ALLOC(h->Utmp, (size_t)n * KMAX);
     ALLOC(h->vtmp, n);
     h->ldf = (n + 3) / 4 * 4;
-    ALLOC(h->Ahi, (size_t)n * h->ldf);
-    ALLOC(h->Alo, (size_t)n * h->ldf);
-    ALLOC(h->vsplit, (size_t)2 * h->ldf);
+    if (h->dd) {
+        DdState& d = h->ddst;
+        d.nblk = (int)((n + DD_BLOCK - 1) / DD_BLOCK);
+        ALLOC(d.DL, (size_t)d.nblk * DD_BLOCK * DD_BLOCK);
+        ALLOC(d.DU, (size_t)d.nblk * DD_BLOCK * DD_BLOCK);
+        ALLOC(d.z, n);
+        ALLOC(d.y1, n);
+        ALLOC(d.y2, n);
+        ALLOC(d.w, n);
+        ALLOC(d.part, dd_part_len(n));
+        ALLOC(d.ready, d.nblk);
+    } else {
+        // the float-float split of A, used only by the float-float operator
+        ALLOC(h->Ahi, (size_t)n * h->ldf);
+        ALLOC(h->Alo, (size_t)n * h->ldf);
+        ALLOC(h->vsplit, (size_t)2 * h->ldf);
+    }
     ALLOC(h->r, n);
     ALLOC(h->dvec, n);
     ALLOC(h->cvec, n);
@@ -748,7 +780,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     // (latency-bound) factorization, on few CTAs so that the panel clusters still find free SMs
     cudaStream_t s_aux = nullptr;
     cudaEvent_t ev_aux = nullptr;
-    if (st == GIR_OK) {
+    if (st == GIR_OK && !h->dd) {
         int lo_prio = 0, hi_prio = 0;
         cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
         if (cudaStreamCreateWithPriority(&s_aux, cudaStreamNonBlocking, lo_prio) != cudaSuccess ||
@@ -769,6 +801,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     }
     if (s_aux) cudaStreamDestroy(s_aux);
     if (st == GIR_OK) st = trsv_setup(h->trsv, h->LU, h->ldl, n, h->fmt, s);
+    if (st == GIR_OK && h->dd) st = dd_setup(h->ddst, h->trsv, s);
     cudaFreeAsync(W, s);
     cudaFreeAsync(colmax, s);
     cudaFreeAsync(UT, s);

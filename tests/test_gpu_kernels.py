@@ -120,9 +120,9 @@ def test_trailing_update(G, fmt, tdt, M, N, K, tc):
     assert bool(((Cm.double() - ref).abs() <= bound).all())
 
 
-def _gpu_factors(G, A, fmt, m=20, k=5):
+def _gpu_factors(G, A, fmt, m=20, k=5, ua="fp64"):
     import paper_2201_09827_gb300 as pkg
-    F = pkg.Factorization(cuda(A), pkg.Params(uf=fmt, m=m, k=k))
+    F = pkg.Factorization(cuda(A), pkg.Params(uf=fmt, m=m, k=k, ua=ua))
     LU, ipiv, R, S, mu = F.export_factors()
     LU = LU.double().cpu().numpy()
     n = A.shape[0]
@@ -180,6 +180,27 @@ def test_apply_minv_and_atilde(G, n, fmt):
         w = F.apply_atilde(cuda(A), cuda(v), trans=trans).cpu().numpy()
         wo = olu.apply_atilde_t(A, Fg, v) if trans else olu.apply_atilde(A, Fg, v)
         assert np.abs(w - wo).max() <= 1e-14 * kappa * np.abs(wo).max()
+    F.close()
+
+
+@pytest.mark.parametrize("n,fmt", [(33, "bf16"), (300, "fp16"), (1001, "bf16")])
+def test_apply_minv_and_atilde_dd(G, n, fmt):
+    """u_a = double-double (the paper's u^2 for u = FP64): M^-1 v, M^-1 A v and their transposes
+    against the oracle's double-double substitution on the same factors. Both carry about 106
+    bits (times the conditioning of the factors, kappa_2(A) = 1e6 here), so the results, rounded
+    to FP64, agree elementwise to a couple of ulps; n = 33 and 1001 leave ragged 32-row blocks."""
+    A = randsvd(n, 1e6, seed=9)
+    F, Fg = _gpu_factors(G, A, fmt, ua="dd")
+    rng = np.random.default_rng(10)
+    u = UNIT_ROUNDOFF["fp64"]
+    for trans in (False, True):
+        v = rng.standard_normal(n)
+        w = F.apply_minv(cuda(v), trans=trans).cpu().numpy()
+        wo = olu.apply_minv_t(Fg, v, "dd") if trans else olu.apply_minv(Fg, v, "dd")
+        assert np.all(np.abs(w - wo) <= 4 * u * np.abs(wo)), np.abs((w - wo) / wo).max()
+        w = F.apply_atilde(cuda(A), cuda(v), trans=trans).cpu().numpy()
+        wo = olu.apply_atilde_t(A, Fg, v, "dd") if trans else olu.apply_atilde(A, Fg, v, "dd")
+        assert np.all(np.abs(w - wo) <= 4 * u * np.abs(wo)), np.abs((w - wo) / wo).max()
     F.close()
 
 

@@ -40,19 +40,20 @@ def gpu_factors_for_oracle(F, n, uf):
 
 
 def run_both(pkg, A, b, uf, u, ur, m, k, tau, imax=10, target=None, max_its=None, carry=1, same_factors=False,
-             flags=0, solver="gcrodr", stop="berr", k_mode="fixed"):
+             flags=0, solver="gcrodr", stop="berr", k_mode="fixed", ua_dd=False):
     """GPU solve and oracle solve. same_factors=True gives the oracle the GPU's u_f factors, which
     isolates the refinement/GCRO-DR part for problems whose iteration counts are sensitive to the
     FP32 summation order of the factorization (poor preconditioners, kappa * u_f >> 1)."""
     prm = pkg.Params(uf=uf, u=u, ur=ur, m=m, k=k, tau=tau, imax=imax,
                      target_berr=-1.0 if target is None else target, carry_mode=carry,
-                     max_its=max_its or 0, flags=flags)
+                     max_its=max_its or 0, flags=flags, ua="dd" if ua_dd else "fp64")
     F = pkg.Factorization(cuda(A), prm)
     x, info = F.solve(cuda(A), cuda(b))
     x = x.cpu().numpy()
     Fo = gpu_factors_for_oracle(F, A.shape[0], uf) if same_factors else None
     F.close()
-    op = OP(uf=uf, u=u, ur=ur, ua="u" if u == "fp64" else "u2", m=m, k=k, tau=tau, imax=imax, target=target,
+    op = OP(uf=uf, u=u, ur=ur, ua="u2" if (ua_dd or u != "fp64") else "u", m=m, k=k, tau=tau, imax=imax,
+            target=target,
             lu_w=32, max_its=max_its or 20 * m, carry_mode=carry, solver=solver, stop=stop, k_mode=k_mode)
     xo, io, _, _ = osolve(A, b, op, F=Fo)
     return x, info, xo, io
@@ -459,3 +460,27 @@ def test_adaptive_k_parity(pkg):
     assert_parity(A, b, x, info, xo, io, "fp64")
     x10, i10, _, _ = run_both(pkg, A, b, "bf16", "fp64", "fp64", 100, 10, 1e-8, target=1e-15, same_factors=True)
     assert info.total_its < 0.85 * i10.total_its
+
+
+@pytest.mark.parametrize("case", ["randsvd", "prolate"])
+def test_dd_operator_solve_parity(pkg, case):
+    """u_a = double-double (Algorithm 4's u^2 for u = FP64) end to end against the oracle's u2 run on
+    the same factors: a randsvd system with the headline precisions at n = 513 (17 blocks of 32
+    rows, the last ragged), and prolate (n = 200, alpha = 0.475, kappa_inf = 6e12) with
+    (fp16, fp64, dd) as in Table 10 (oracle, own factors: 18 (13,5)). Closer to singular
+    (alpha = 0.465, kappa_inf = 3e16) the step counts depend on the rounding of the factors and
+    neither run is a reference for the other."""
+    if case == "randsvd":
+        n = 513
+        A = randsvd(n, 1e3, seed=0)
+        b = A @ normal_vector(n, 2)
+        x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 50, 10, 1e-8, target=1e-15,
+                                   same_factors=True, ua_dd=True)
+        assert normwise_berr(A, x, b) <= 1e-15
+    else:
+        A = prolate(200, 0.475)
+        b = np.ones(200)
+        x, info, xo, io = run_both(pkg, A, b, "fp16", "fp64", "dd", 100, 10, 1e-8, target=1e-15, max_its=400,
+                                   same_factors=True, ua_dd=True)
+    assert info.status == 0 and io.converged
+    assert_parity(A, b, x, info, xo, io, "fp64")
