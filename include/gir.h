@@ -186,6 +186,13 @@ gir_status gir_residual(const double* A, int64_t n, int64_t lda, const double* x
 gir_status gir_backward_errors(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
                                gir_prec prec, double* eta, double* omega, void* stream);
 
+/* Failure-detection check of the bounded device waits: runs one block of a triangular solve
+ * whose dependency is never published, so its wait gives up after spin_limit polls
+ * (1 <= spin_limit <= 2e7; about 1e5 polls take a fraction of a second). Returns GIR_TIMEOUT when
+ * the kernel reported the timeout and returned (the expected outcome; the context stays
+ * usable), GIR_OK if it did not, GIR_INVALID_ARG or GIR_CUDA_ERROR. Synchronises the stream. */
+gir_status gir_selftest_wait_timeout(long long spin_limit, void* stream);
+
 /* w = A v (trans = 0) or w = A^T v (trans = 1) in FP64 arithmetic (device pointers). */
 gir_status gir_gemv(const double* A, int64_t n, int64_t lda, const double* v, double* w,
                     int trans, void* stream);

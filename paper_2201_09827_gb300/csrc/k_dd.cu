@@ -101,11 +101,16 @@ __global__ void __launch_bounds__(256) k_gemv_dd(const double* __restrict__ A, i
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const double* row = A + i * lda;
         double sh = 0.0, sl = 0.0;
+        // high parts summed by TwoSum; product and sum errors collected in sl, normalised once
         for (int64_t j = lane; j < n; j += 32) {
             const double a = __ldcs(row + j), x = __ldg(v + j);
             const double p = a * x;
-            dd_acc(sh, sl, p, fma(a, x, -p));
+            double hs, ht;
+            two_sum(sh, p, hs, ht);
+            sh = hs;
+            sl += ht + fma(a, x, -p);
         }
+        fast_two_sum(sh, sl, sh, sl);
         dd_warp_reduce(sh, sl);
         if (lane == 0) w[i] = make_double2(sh, sl);
     }
@@ -121,8 +126,12 @@ __global__ void __launch_bounds__(256) k_gemv_t_dd_partial(const double* __restr
     for (int64_t i = i0; i < i1; ++i) {
         const double a = __ldcs(A + i * lda + j), x = __ldg(v + i);
         const double p = a * x;
-        dd_acc(sh, sl, p, fma(a, x, -p));
+        double hs, ht;
+        two_sum(sh, p, hs, ht);
+        sh = hs;
+        sl += ht + fma(a, x, -p);
     }
+    fast_two_sum(sh, sl, sh, sl);
     part[(int64_t)blockIdx.y * n + j] = make_double2(sh, sl);
 }
 __global__ void k_sum_parts_dd(const double2* __restrict__ part, int nparts, int64_t n, double2* __restrict__ w) {
@@ -197,15 +206,6 @@ __global__ void __launch_bounds__(DB) k_diag_inv_dd(const uint16_t* __restrict__
     for (int i = 0; i < DB; ++i) D[(base + i) * DB + c] = make_double2(Xh[i][c], Xl[i][c]);
 }
 
-gir_status dd_setup(DdState& dd, const TrsvState& st, cudaStream_t s) {
-    count_launch(), k_diag_inv_dd<<<dd.nblk, DB, 0, s>>>(st.LU, st.ldl, st.n, st.fmt, 0, dd.DL);
-    count_launch(), k_diag_inv_dd<<<dd.nblk, DB, 0, s>>>(st.LU, st.ldl, st.n, st.fmt, 1, dd.DU);
-    GIR_CUDA_TRY(cudaMemsetAsync(dd.ready, 0, (size_t)dd.nblk * sizeof(int), s));
-    dd.epoch = 0;
-    GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
-}
-
 // ------------------------------------------------------------------ persistent block solve
 __device__ __forceinline__ int dd_ld_acquire(const int* p) {
     int v;
@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(DT) k_trsv_dd(const uint16_t* __restrict__ LU,
                                                 const double2* __restrict__ zin, double2* yout,
                                                 int* ready, int epoch,
                                                 unsigned long long* __restrict__ ticket_ctr, unsigned long long base,
-                                                int* __restrict__ abort_flag, int* __restrict__ flags) {
+                                                int* __restrict__ abort_flag, int* __restrict__ flags,
+                                                long long spin_limit) {
     __shared__ double2 yj[2][DB];
     __shared__ double2 accs[DB];
     __shared__ int s_ticket, s_abort;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(DT) k_trsv_dd(const uint16_t* __restrict__ LU,
                 bool ok = true;
                 while (dd_ld_acquire(ready + J) != epoch) {
                     if (((spins & 1023) == 0) && dd_ld_acquire(abort_flag)) { ok = false; break; }
-                    if (++spins > SPIN_LIMIT) {
+                    if (++spins > spin_limit) {
                         atomicOr(flags, DEV_TIMEOUT);
                         atomicExch(abort_flag, 1);
                         ok = false;
@@ -287,12 +288,21 @@ __global__ void __launch_bounds__(DT) k_trsv_dd(const uint16_t* __restrict__ LU,
         }
         __syncthreads();
         if (s_abort) break;
+        // 8 terms: exact high products summed by TwoSum, the low parts collected unnormalised
         double sh = 0.0, sl = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const double2 y = yj[buf][q * 8 + c];
-            dd_mac_d(sh, sl, tv[c], y.x, y.y);
+            const double a = tv[c];
+            const double p = a * y.x;
+            double e = fma(a, y.x, -p);
+            e = fma(a, y.y, e);
+            double hs, ht;
+            two_sum(sh, p, hs, ht);
+            sh = hs;
+            sl += ht + e;
         }
+        fast_two_sum(sh, sl, sh, sl);
         dd_quad_reduce(sh, sl);
         dd_acc(ah, al, -sh, -sl);
     }
@@ -318,6 +328,31 @@ __global__ void __launch_bounds__(DT) k_trsv_dd(const uint16_t* __restrict__ LU,
         __threadfence();
         dd_st_release(ready + I, epoch);
     }
+}
+
+// The solve CTAs reserve more than half of an SM's shared memory so that each runs alone on its
+// SM: the FP64 pipe is the bottleneck, and a CTA on the critical path (the block next in the
+// chain) must not share it with CTAs that are working ahead on off-diagonal tiles. CTAs beyond
+// the SM count start as earlier ones finish and draw later tickets.
+static int solo_smem_bytes() {
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    return per_sm / 2 + 1024;
+}
+
+gir_status dd_setup(DdState& dd, const TrsvState& st, cudaStream_t s) {
+    dd.solo_smem = solo_smem_bytes();
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_dd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dd.solo_smem));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_dd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dd.solo_smem));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_dd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dd.solo_smem));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_dd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dd.solo_smem));
+    count_launch(), k_diag_inv_dd<<<dd.nblk, DB, 0, s>>>(st.LU, st.ldl, st.n, st.fmt, 0, dd.DL);
+    count_launch(), k_diag_inv_dd<<<dd.nblk, DB, 0, s>>>(st.LU, st.ldl, st.n, st.fmt, 1, dd.DU);
+    GIR_CUDA_TRY(cudaMemsetAsync(dd.ready, 0, (size_t)dd.nblk * sizeof(int), s));
+    dd.epoch = 0;
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
 }
 
 // ------------------------------------------------------------------ pre/post scaling
@@ -369,9 +404,9 @@ static gir_status run_trsv_dd(DdState& dd, TrsvState& st, const double2* D, cons
     st.tickets += (unsigned long long)dd.nblk;
     const int epoch = ++dd.epoch;
     const int tslot = trace_begin(s);
-    count_launch(), k_trsv_dd<LOWER, TRANS><<<dd.nblk, DT, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, dd.nblk, z, y,
+    count_launch(), k_trsv_dd<LOWER, TRANS><<<dd.nblk, DT, dd.solo_smem, s>>>(st.LU, st.ldl, st.fmt, D, st.n, dd.nblk, z, y,
                                                                    dd.ready, epoch, st.ticket_ctr, base,
-                                                                   st.abort_flag, flags);
+                                                                   st.abort_flag, flags, SPIN_LIMIT);
     trace_end(tslot, "trsv dd", s);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
@@ -398,3 +433,45 @@ gir_status apply_minv_dd(DdState& dd, TrsvState& st, const double* w64, double* 
 }
 
 }  // namespace gir
+
+// A bounded wait that runs out: one CTA of the double-double solve takes ticket 1 of a 2-block
+// lower solve whose block 0 never runs, so it polls a publication flag that nothing sets. After
+// spin_limit polls it raises the timeout flag and the abort flag, publishes its block and returns.
+extern "C" gir_status gir_selftest_wait_timeout(long long spin_limit, void* stream) {
+    using namespace gir;
+    if (spin_limit < 1 || spin_limit > SPIN_LIMIT) return GIR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = 2 * DB;
+    // one allocation: LU (n x n u16) | D (2 blocks) | z | y | ready | flags, abort | ticket
+    const size_t off_D = (size_t)n * n * sizeof(uint16_t);
+    const size_t off_z = off_D + 2 * DB * DB * sizeof(double2);
+    const size_t off_y = off_z + n * sizeof(double2);
+    const size_t off_r = off_y + n * sizeof(double2);
+    const size_t off_t = off_r + 8 * sizeof(int);
+    const size_t bytes = off_t + sizeof(unsigned long long);
+    char* buf = nullptr;
+    GIR_CUDA_TRY(cudaMalloc(&buf, bytes));
+    gir_status st = GIR_OK;
+    int hflags = 0;
+    if (cudaMemsetAsync(buf, 0, bytes, s) != cudaSuccess) st = GIR_CUDA_ERROR;
+    int* ready = reinterpret_cast<int*>(buf + off_r);
+    int* flags = ready + 2;
+    int* abort_flag = ready + 4;
+    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(buf + off_t);
+    if (st == GIR_OK) {
+        // base = -1: the single CTA draws ticket 1, i.e. block 1, which depends on block 0
+        k_trsv_dd<true, false><<<1, DT, 0, s>>>(reinterpret_cast<const uint16_t*>(buf), n, FF_BF16,
+                                                reinterpret_cast<const double2*>(buf + off_D), n, 2,
+                                                reinterpret_cast<const double2*>(buf + off_z),
+                                                reinterpret_cast<double2*>(buf + off_y), ready, 1, ticket,
+                                                ~0ULL, abort_flag, flags, spin_limit);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) st = GIR_CUDA_ERROR;
+    }
+    if (st == GIR_OK && cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = GIR_CUDA_ERROR;
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == GIR_OK) st = GIR_CUDA_ERROR;
+    cudaFree(buf);
+    if (st != GIR_OK) return st;
+    return (hflags & DEV_TIMEOUT) ? GIR_TIMEOUT : GIR_OK;
+}

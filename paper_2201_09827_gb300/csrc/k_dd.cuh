@@ -20,6 +20,7 @@ struct DdState {
     double2* part = nullptr;      // partial sums of A^T v: ceil(n / DD_TROWS) x n
     int* ready = nullptr;         // per-block publication epochs of the solves
     int epoch = 0;
+    int solo_smem = 0;            // dynamic shared memory of a solve CTA (one CTA per SM)
 };
 
 size_t dd_part_len(int64_t n);

@@ -57,6 +57,7 @@ SYMBOLS = {
                                C.c_void_p]),
     "gir_backward_errors": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
+    "gir_selftest_wait_timeout": (C.c_int, [C.c_longlong, C.c_void_p]),
     "gir_gemv": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "gir_export_factors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.POINTER(C.c_double), C.c_void_p]),
@@ -308,6 +309,11 @@ def backward_errors(A, x, b, prec="fp64", stream=None):
     if st != GIR_OK:
         raise GirError(st, "gir_backward_errors")
     return eta.value, om.value
+
+
+def selftest_wait_timeout(spin_limit=100000, stream=None):
+    """Status of a device wait made to run out (GIR_TIMEOUT is the expected answer)."""
+    return load().gir_selftest_wait_timeout(int(spin_limit), _stream(stream))
 
 
 def gemv(A, v, trans=False, stream=None):

@@ -484,3 +484,18 @@ def test_dd_operator_solve_parity(pkg, case):
                                    same_factors=True, ua_dd=True)
     assert info.status == 0 and io.converged
     assert_parity(A, b, x, info, xo, io, "fp64")
+
+
+def test_bounded_wait_times_out_and_context_survives(pkg):
+    """A device wait on a flag that nothing sets gives up after its poll limit, reports
+    GIR_TIMEOUT through the status flags and returns; the next solve runs normally."""
+    from paper_2201_09827_gb300 import gir
+    import time
+    t0 = time.time()
+    assert gir.selftest_wait_timeout(100000) == gir.GIR_TIMEOUT
+    assert time.time() - t0 < 30.0
+    assert gir.selftest_wait_timeout(0) == gir.GIR_INVALID_ARG
+    A = randsvd(128, 1e2, seed=1)
+    b = rhs_uniform(128, 1)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 20, 4, 1e-8, target=1e-15)
+    assert info.status == gir.GIR_OK
