@@ -5,10 +5,11 @@
 //    the pencil G^T G z = theta G^T W^T V z, reduced to the standard problem of
 //    R_G^-1 Q_G^T (W^T V) with G = Q_G R_G), eigenvector selection and QR(G P_k);
 //  * Cholesky of the Gram matrix for the QR of A~ Y~ (carry to the next system).
-// Eigenvalues: Householder reduction to Hessenberg form and Francis double-shift QR;
-// eigenvectors of the selected eigenvalues by inverse iteration on the Hessenberg matrix.
-// All loops over rows/columns are split across the 32 lanes; scalar parts are computed
-// redundantly by every lane from shared memory.
+// Eigenvalues: Householder reduction to Hessenberg form (FP64) and Francis double-shift QR on
+// an FP32 copy (the eigenvalues only steer the selection and the shifts); eigenvectors of the
+// selected eigenvalues by FP64 inverse iteration on the Hessenberg matrix, one warp per
+// eigenvalue. All loops over rows/columns are split across the 32 lanes of a warp; scalar parts
+// are computed redundantly by every lane from shared memory.
 #include "gir_internal.cuh"
 #include "k_small.cuh"
 
@@ -211,21 +212,32 @@ __device__ void hess_reduce(double* M, int ld, int d, double* Qh, double* v) {
 // QR iteration with deflation on negligible subdiagonal entries and exceptional shifts after
 // 10 and 20 iterations without deflation. Conjugate pairs are stored as (re, +im), (re, -im).
 // Returns 0 on success, 1 if some eigenvalue needed more than 60 iterations.
-__device__ int hqr_eigs(double* a, int ld, int d, double* wr, double* wi) {
+// T = float: the eigenvalues only choose the shifts of the FP64 inverse iteration and the
+// selection, and GB300 issues FP32 scalar chains about 15 times faster than FP64 ones.
+template <typename T>
+__device__ T sgnT(T a, T b) { return b >= T(0) ? fabs(a) : -fabs(a); }
+template <typename T>
+__device__ T wsumT(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ int hqr_eigs(T* a, int ld, int d, T* wr, T* wi) {
     const int lane = LANE;
 #define A_(i, j) a[(i) + (j) * ld]
-    double anorm = 0.0;
+    T anorm = 0;
     for (int i = lane; i < d; i += 32)
         for (int j = max(i - 1, 0); j < d; ++j) anorm += fabs(A_(i, j));
-    anorm = wsum(anorm);
+    anorm = wsumT(anorm);
     int nn = d - 1;
-    double t = 0.0;
+    T t = 0;
     int fail = 0;
     while (nn >= 0) {
         int its = 0, l;
         do {
             for (l = nn; l >= 1; --l) {
-                double s = fabs(A_(l - 1, l - 1)) + fabs(A_(l, l));
+                T s = fabs(A_(l - 1, l - 1)) + fabs(A_(l, l));
                 if (s == 0.0) s = anorm;
                 if (fabs(A_(l, l - 1)) + s == s) {
                     WSYNC();
@@ -234,24 +246,24 @@ __device__ int hqr_eigs(double* a, int ld, int d, double* wr, double* wi) {
                     break;
                 }
             }
-            double x = A_(nn, nn);
+            T x = A_(nn, nn);
             if (l == nn) {
                 if (lane == 0) { wr[nn] = x + t; wi[nn] = 0.0; }
                 nn--;
             } else {
-                double y = A_(nn - 1, nn - 1);
-                double w = A_(nn, nn - 1) * A_(nn - 1, nn);
+                T y = A_(nn - 1, nn - 1);
+                T w = A_(nn, nn - 1) * A_(nn - 1, nn);
                 if (l == nn - 1) {
-                    double p = 0.5 * (y - x);
-                    double q = p * p + w;
-                    double z = sqrt(fabs(q));
+                    T p = T(0.5) * (y - x);
+                    T q = p * p + w;
+                    T z = sqrt(fabs(q));
                     x += t;
                     if (q >= 0.0) {
-                        z = p + sgn(z, p);
+                        z = p + sgnT(z, p);
                         if (lane == 0) {
                             wr[nn - 1] = wr[nn] = x + z;
                             if (z != 0.0) wr[nn] = x - w / z;
-                            wi[nn - 1] = wi[nn] = 0.0;
+                            wi[nn - 1] = wi[nn] = T(0);
                         }
                     } else {
                         if (lane == 0) {
@@ -266,7 +278,7 @@ __device__ int hqr_eigs(double* a, int ld, int d, double* wr, double* wi) {
                         fail = 1;
                         // give up on this block: report the diagonal entries as eigenvalues
                         if (lane == 0)
-                            for (int i = l; i <= nn; ++i) { wr[i] = A_(i, i) + t; wi[i] = 0.0; }
+                            for (int i = l; i <= nn; ++i) { wr[i] = A_(i, i) + t; wi[i] = T(0); }
                         nn = l - 1;
                         break;
                     }
@@ -275,46 +287,47 @@ __device__ int hqr_eigs(double* a, int ld, int d, double* wr, double* wi) {
                         WSYNC();
                         for (int i = lane; i <= nn; i += 32) A_(i, i) -= x;
                         WSYNC();
-                        double s = fabs(A_(nn, nn - 1)) + fabs(A_(nn - 1, nn - 2));
-                        x = y = 0.75 * s;
-                        w = -0.4375 * s * s;
+                        T s = fabs(A_(nn, nn - 1)) + fabs(A_(nn - 1, nn - 2));
+                        x = y = T(0.75) * s;
+                        w = T(-0.4375) * s * s;
                     }
                     ++its;
                     int m;
-                    double p = 0, q = 0, r = 0, z;
+                    T p = 0, q = 0, r = 0, z;
                     for (m = nn - 2; m >= l; --m) {
                         z = A_(m, m);
                         r = x - z;
-                        double s = y - z;
+                        T s = y - z;
                         p = (r * s - w) / A_(m + 1, m) + A_(m, m + 1);
                         q = A_(m + 1, m + 1) - z - r - s;
                         r = A_(m + 2, m + 1);
                         s = fabs(p) + fabs(q) + fabs(r);
-                        p /= s;
-                        q /= s;
-                        r /= s;
+                        const T is = T(1) / s;
+                        p *= is;
+                        q *= is;
+                        r *= is;
                         if (m == l) break;
-                        double u = fabs(A_(m, m - 1)) * (fabs(q) + fabs(r));
-                        double v = fabs(p) * (fabs(A_(m - 1, m - 1)) + fabs(z) + fabs(A_(m + 1, m + 1)));
+                        T u = fabs(A_(m, m - 1)) * (fabs(q) + fabs(r));
+                        T v = fabs(p) * (fabs(A_(m - 1, m - 1)) + fabs(z) + fabs(A_(m + 1, m + 1)));
                         if (u + v == v) break;
                     }
                     WSYNC();
                     if (lane == 0)
                         for (int i = m + 2; i <= nn; ++i) {
-                            A_(i, i - 2) = 0.0;
-                            if (i != m + 2) A_(i, i - 3) = 0.0;
+                            A_(i, i - 2) = T(0);
+                            if (i != m + 2) A_(i, i - 3) = T(0);
                         }
                     WSYNC();
                     for (int k = m; k <= nn - 1; ++k) {
                         if (k != m) {
                             p = A_(k, k - 1);
                             q = A_(k + 1, k - 1);
-                            r = (k != nn - 1) ? A_(k + 2, k - 1) : 0.0;
+                            r = (k != nn - 1) ? A_(k + 2, k - 1) : T(0);
                             x = fabs(p) + fabs(q) + fabs(r);
-                            if (x != 0.0) { p /= x; q /= x; r /= x; }
+                            if (x != T(0)) { const T ix = T(1) / x; p *= ix; q *= ix; r *= ix; }
                         }
-                        double s = sgn(sqrt(p * p + q * q + r * r), p);
-                        if (s != 0.0) {
+                        T s = sgnT(T(sqrt(p * p + q * q + r * r)), p);
+                        if (s != T(0)) {
                             WSYNC();
                             if (lane == 0) {
                                 if (k == m) {
@@ -324,14 +337,15 @@ __device__ int hqr_eigs(double* a, int ld, int d, double* wr, double* wi) {
                                 }
                             }
                             p += s;
-                            x = p / s;
-                            y = q / s;
-                            z = r / s;
-                            q /= p;
-                            r /= p;
+                            const T is = T(1) / s, ip = T(1) / p;
+                            x = p * is;
+                            y = q * is;
+                            z = r * is;
+                            q *= ip;
+                            r *= ip;
                             WSYNC();
                             for (int jj = k + lane; jj <= nn; jj += 32) {
-                                double pp = A_(k, jj) + q * A_(k + 1, jj);
+                                T pp = A_(k, jj) + q * A_(k + 1, jj);
                                 if (k != nn - 1) {
                                     pp += r * A_(k + 2, jj);
                                     A_(k + 2, jj) -= pp * z;
@@ -342,7 +356,7 @@ __device__ int hqr_eigs(double* a, int ld, int d, double* wr, double* wi) {
                             WSYNC();
                             int mmin = nn < k + 3 ? nn : k + 3;
                             for (int i = l + lane; i <= mmin; i += 32) {
-                                double pp = x * A_(i, k) + y * A_(i, k + 1);
+                                T pp = x * A_(i, k) + y * A_(i, k + 1);
                                 if (k != nn - 1) {
                                     pp += z * A_(i, k + 2);
                                     A_(i, k + 2) -= pp * r;
@@ -394,7 +408,8 @@ __device__ void inv_iter(const double* Hm, int ld, int d, double lr, double li, 
         double orr = sw ? ar : nr_k, oi = sw ? ai : ni_k;
         double den = pr * pr + pi * pi;
         if (den == 0.0) { pr = eps; pi = 0.0; den = eps * eps; }
-        double lre = (orr * pr + oi * pi) / den, lim = (oi * pr - orr * pi) / den;
+        const double iden = 1.0 / den;
+        double lre = (orr * pr + oi * pi) * iden, lim = (oi * pr - orr * pi) * iden;
         if (lane == 0) { mr[k] = lre; mi[k] = lim; swp[k] = sw ? 1 : 0; }
         for (int j = k + lane; j < d; j += 32) {
             double hr = Hm[(k + 1) + j * ld] - ((j == k + 1) ? lr : 0.0);
@@ -446,9 +461,9 @@ __device__ void inv_iter(const double* Hm, int ld, int d, double lr, double li, 
             if (lane == 0) {
                 double br = xr[i] - sr, bi = xi[i] - si;
                 double ur = U[UP(i, i)], ui = U[UP(i, i) + 1];
-                double den = ur * ur + ui * ui;
-                xr[i] = (br * ur + bi * ui) / den;
-                xi[i] = (bi * ur - br * ui) / den;
+                const double iden = 1.0 / (ur * ur + ui * ui);
+                xr[i] = (br * ur + bi * ui) * iden;
+                xi[i] = (bi * ur - br * ui) * iden;
             }
             WSYNC();
         }
@@ -518,41 +533,77 @@ __device__ int select_eigs(const double* wr, const double* wi, int d, int k, int
     return cols;
 }
 
-// Eigen-decomposition driver on shared memory: M (d x d, ld d, overwritten by its Hessenberg
-// form), W (workspace >= d*d + 2d doubles... and complex rows), Qh global d x d. Produces a real
-// basis P (d x cols, ld ldp, global) of the selected eigenvectors. Returns cols.
-__device__ int eig_select(double* M, double* Wk, int d, int k, int largest, int mcap, double* Qh, double* P, int ldp,
-                          double* wr, double* wi, double* vec, double* xr, double* xi, double* mr, double* mi, int* swp,
-                          double* cr, double* ci, int* fail_out) {
+// Eigenvalues and selection (one warp): Householder reduction of M (d x d, ld d, FP64, in place)
+// to Hessenberg form with the similarity accumulated in Qh (global, ld d); eigenvalues of a
+// power-of-two scaled FP32 copy (Af, d*d floats) by Francis QR; the selected eigenvalues in
+// sel[0..nsel) with the first basis column of each in colofs[]. Returns the number of columns.
+__device__ int eig_values(double* M, float* Af, int d, int k, int largest, int mcap, double* Qh, double* wr,
+                          double* wi, double* vec, int* sel, int* colofs, int* nsel_out, double* hn_out,
+                          int* fail_out) {
     const int lane = LANE;
+    __shared__ float wrf[SM_DMAX], wif[SM_DMAX];
+    __shared__ int nsel_s, cols_s;
     hess_reduce(M, d, d, Qh, vec);
     double hn = 0.0;
     for (int e = lane; e < d * d; e += 32) hn = fmax(hn, fabs(M[e]));
     hn = warp_max(hn);
-    for (int e = lane; e < d * d; e += 32) Wk[e] = M[e];
+    // scale by 2^-e with hn 2^-e in [0.5, 1): no FP32 overflow, and the unscaling is exact
+    int ex = 0;
+    if (hn > 0.0 && hn < 1.7976931348623157e308) frexp(hn, &ex);
+    const double sc = ldexp(1.0, -ex);
+    for (int e = lane; e < d * d; e += 32) Af[e] = (float)(M[e] * sc);
     WSYNC();
-    int fail = hqr_eigs(Wk, d, d, wr, wi);
-    *fail_out = fail;
-    __shared__ int sel[SM_DMAX];
-    __shared__ int nsel_s, cols_s;
-    if (lane == 0) {
-        int ns;
-        int cols = select_eigs(wr, wi, d, k, largest, mcap, sel, &ns);
-        nsel_s = ns;
-        cols_s = cols;
+    *fail_out = hqr_eigs<float>(Af, d, d, wrf, wif);
+    for (int i = lane; i < d; i += 32) {
+        wr[i] = (double)wrf[i] / sc;
+        wi[i] = (double)wif[i] / sc;
     }
     WSYNC();
-    const int nsel = nsel_s;
-    int col = 0;
-    for (int t = 0; t < nsel; ++t) {
-        int i = sel[t];
-        double lr = wr[i], li = fabs(wi[i]);
-        inv_iter(M, d, d, lr, li, hn, Wk, xr, xi, mr, mi, swp, cr, ci);
-        // z = Qh x
+    if (lane == 0) {
+        int ns;
+        cols_s = select_eigs(wr, wi, d, k, largest, mcap, sel, &ns);
+        nsel_s = ns;
+        int c = 0;
+        for (int t = 0; t < ns; ++t) {
+            colofs[t] = c;
+            c += (wi[sel[t]] != 0.0) ? 2 : 1;
+        }
+    }
+    WSYNC();
+    *nsel_out = nsel_s;
+    *hn_out = hn;
+    return cols_s;
+}
+
+// Doubles of shared workspace per warp for eig_vectors.
+__host__ __device__ inline int eigvec_stride(int d) { return d * (d + 1) + 7 * d; }
+
+// Eigenvectors of the selected eigenvalues (all warps of the CTA, nw of them with a workspace
+// each in wbuf): FP64 inverse iteration on the Hessenberg matrix M from the eigenvalue as shift,
+// then z = Qh x into the real basis P (d x cols, ld ldp): a real eigenvalue gives one column, a
+// conjugate pair the real and imaginary parts.
+__device__ void eig_vectors(const double* M, int d, const double* Qh, double* P, int ldp, const double* wr,
+                            const double* wi, const int* sel, const int* colofs, int nsel, double hn, double* wbuf,
+                            int nw) {
+    const int lane = LANE, warp = threadIdx.x >> 5;
+    if (warp >= nw) return;
+    double* U = wbuf + (size_t)warp * eigvec_stride(d);
+    double* xr = U + d * (d + 1);
+    double* xi = xr + d;
+    double* mr = xi + d;
+    double* mi = mr + d;
+    double* cr = mi + d;
+    double* ci = cr + d;
+    int* swp = reinterpret_cast<int*>(ci + d);
+    for (int t = warp; t < nsel; t += nw) {
+        const int i = sel[t];
+        const double lr = wr[i], li = fabs(wi[i]);
+        inv_iter(M, d, d, lr, li, hn, U, xr, xi, mr, mi, swp, cr, ci);
+        const int col = colofs[t];
         for (int r = lane; r < d; r += 32) {
             double zr = 0.0, zi = 0.0;
             for (int c = 0; c < d; ++c) {
-                double q = Qh[r + c * d];
+                const double q = Qh[r + c * d];
                 zr += q * xr[c];
                 zi += q * xi[c];
             }
@@ -560,25 +611,39 @@ __device__ int eig_select(double* M, double* Wk, int d, int k, int largest, int 
             if (li != 0.0) P[r + (col + 1) * ldp] = zi;
         }
         WSYNC();
-        col += (li != 0.0) ? 2 : 1;
     }
-    return col;
 }
 
 // ------------------------------------------------------------------ cycle end
 // Dynamic shared memory layout: M [(d+1)*d], Wk [2*d*d + 4*d] (G / hqr copy / inverse-iteration rows).
-__global__ void __launch_bounds__(32) k_cycle_close(SmallState* st, double* Qh, double* Pbuf, double* Gq) {
+constexpr int CLOSE_THREADS = 128;
+constexpr int CLOSE_SMEM_DOUBLES = 210 * 1024 / 8;
+
+// Warps that get an inverse-iteration workspace behind the (d+1) x d block M.
+__host__ __device__ inline int eigvec_warps(int d, int mrows) {
+    const int avail = CLOSE_SMEM_DOUBLES - mrows * d;
+    int nw = avail / eigvec_stride(d);
+    nw = nw > CLOSE_THREADS / 32 ? CLOSE_THREADS / 32 : nw;
+    return nw < 1 ? 1 : nw;
+}
+
+// Warp 0 runs everything but the eigenvectors, which all warps share (one selected eigenvalue
+// each at a time: GB300's FP64 pipes are per SM sub-partition, so four warps are four times one).
+__global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, double* Qh, double* Pbuf, double* Gq) {
     extern __shared__ double smem[];
-    const int lane = LANE;
+    const int lane = LANE, warp = threadIdx.x >> 5;
     const int j = st->j, kc = st->kc, d = kc + j;
     const int first = st->first;
     double* M = smem;                          // (d+1) x d, ld d+1
-    double* Wk = smem + (size_t)(d + 1) * d;   // >= (d+1)*d ... and 2*d*d for inv_iter rows
+    double* Wk = smem + (size_t)(d + 1) * d;   // (d+1) x d doubles; the eigenvector workspaces from here
     __shared__ double y[SM_DMAX], tau[SM_DMAX + 1], wr[SM_DMAX], wi[SM_DMAX], vec[SM_DMAX + 1];
-    __shared__ double xr[SM_DMAX], xi[SM_DMAX], mr[SM_DMAX], mi[SM_DMAX], cr[SM_DMAX], ci[SM_DMAX];
-    __shared__ int swp[SM_DMAX];
-    __shared__ int knew_s;
+    __shared__ int sel[SM_DMAX], colofs[SM_DMAX];
+    __shared__ int nsel_s, cols_s;
+    __shared__ double hn_s;
+    const int k = st->k_target;
+    const bool recycle = (k > 0) && (first ? (j > k) : true) && d >= 1;
 
+    if (warp == 0) {
     // D_k = diag(1 / ||u_i||) from the Gram matrix U^T U (ld kc)
     for (int i = lane; i < kc; i += 32) st->dk[i] = 1.0 / sqrt(st->UtU[i + i * kc]);
     WSYNC();
@@ -613,10 +678,7 @@ __global__ void __launch_bounds__(32) k_cycle_close(SmallState* st, double* Qh, 
     }
     WSYNC();
 
-    int knew = 0;
-    const int k = st->k_target;
-    bool recycle = (k > 0) && (first ? (j > k) : true);
-    if (recycle && d >= 1) {
+    if (recycle) {
         // ---- harmonic Ritz matrix M (d x d, ld d)
         if (first) {
             // M = H_j + h^2 f e_j^T with H_j^T f = e_j (Gaussian elimination with partial pivoting)
@@ -705,11 +767,26 @@ __global__ void __launch_bounds__(32) k_cycle_close(SmallState* st, double* Qh, 
                 WSYNC();
             }
         }
-        int fail = 0;
-        int cols = eig_select(M, Wk, d, k, first ? 0 : 1, st->m, Qh, Pbuf, d, wr, wi, vec, xr, xi, mr, mi, swp, cr,
-                              ci, &fail);
-        if (fail) st->status |= 0;  // non-converged eigenvalues keep the diagonal estimates
+        int fail = 0, nsel = 0;
+        double hn = 0.0;
+        const int cols = eig_values(M, reinterpret_cast<float*>(Wk), d, k, first ? 0 : 1, st->m, Qh, wr, wi, vec, sel,
+                                    colofs, &nsel, &hn, &fail);
+        // non-converged eigenvalues keep their diagonal estimates (fail is not an error)
+        if (lane == 0) {
+            nsel_s = nsel;
+            cols_s = cols;
+            hn_s = hn;
+        }
         for (int i = lane; i < d; i += 32) { st->eig_wr[i] = wr[i]; st->eig_wi[i] = wi[i]; }
+    }
+    }  // warp 0
+    __syncthreads();
+    if (recycle) eig_vectors(M, d, Qh, Pbuf, d, wr, wi, sel, colofs, nsel_s, hn_s, Wk, eigvec_warps(d, d + 1));
+    __syncthreads();
+    if (warp != 0) return;
+    int knew = 0;
+    if (recycle) {
+        int cols = cols_s;
         // ---- G P ((d+1) x cols) in Gq (global), QR with positive diagonal, rank drop
         const int ldg = d + 1;
         for (int e = lane; e < ldg * cols; e += 32) {
@@ -792,15 +869,12 @@ __global__ void __launch_bounds__(32) k_cycle_close(SmallState* st, double* Qh, 
         WSYNC();
         knew = cols;
     }
-    if (lane == 0) {
-        st->knew = knew;
-        knew_s = knew;
-    }
+    if (lane == 0) st->knew = knew;
 }
 
 gir_status launch_cycle_close(SmallState* st, double* qh_scratch, cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = 210 * 1024;
+    const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
     if (!attr) {
         GIR_CUDA_TRY(cudaFuncSetAttribute(k_cycle_close, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
@@ -808,7 +882,7 @@ gir_status launch_cycle_close(SmallState* st, double* qh_scratch, cudaStream_t s
     double* Qh = qh_scratch;
     double* Pbuf = qh_scratch + SM_DMAX * SM_DMAX;
     double* Gq = Pbuf + SM_DMAX * (SM_KMAX + 2);
-    count_launch(), k_cycle_close<<<1, 32, smem, s>>>(st, Qh, Pbuf, Gq);
+    count_launch(), k_cycle_close<<<1, CLOSE_THREADS, smem, s>>>(st, Qh, Pbuf, Gq);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
@@ -874,33 +948,49 @@ gir_status launch_chol_gram(SmallState* st, int k, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ standalone eigen test
-__global__ void __launch_bounds__(32) k_small_eig(const double* Min, int d, int k, int largest, int mcap, double* wr_o,
-                                                  double* wi_o, double* P, int* kout, double* Qh) {
+__global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, int d, int k, int largest, int mcap,
+                                                             double* wr_o, double* wi_o, double* P, int* kout,
+                                                             double* Qh) {
     extern __shared__ double smem[];
-    const int lane = LANE;
+    const int lane = LANE, warp = threadIdx.x >> 5;
     double* M = smem;
-    double* Wk = smem + (size_t)d * d;
+    double* Wk = smem + (size_t)(d + 1) * d;
     __shared__ double wr[SM_DMAX], wi[SM_DMAX], vec[SM_DMAX + 1];
-    __shared__ double xr[SM_DMAX], xi[SM_DMAX], mr[SM_DMAX], mi[SM_DMAX], cr[SM_DMAX], ci[SM_DMAX];
-    __shared__ int swp[SM_DMAX];
-    for (int e = lane; e < d * d; e += 32) M[e] = Min[e];
-    WSYNC();
-    int fail = 0;
-    int cols = eig_select(M, Wk, d, k, largest, mcap, Qh, P, d, wr, wi, vec, xr, xi, mr, mi, swp, cr, ci, &fail);
+    __shared__ int sel[SM_DMAX], colofs[SM_DMAX];
+    __shared__ int nsel_s, cols_s, fail_s;
+    __shared__ double hn_s;
+    if (warp == 0) {
+        for (int e = lane; e < d * d; e += 32) M[e] = Min[e];
+        WSYNC();
+        int fail = 0, nsel = 0;
+        double hn = 0.0;
+        const int cols = eig_values(M, reinterpret_cast<float*>(Wk), d, k, largest, mcap, Qh, wr, wi, vec, sel, colofs,
+                                    &nsel, &hn, &fail);
+        if (lane == 0) {
+            nsel_s = nsel;
+            cols_s = cols;
+            hn_s = hn;
+            fail_s = fail;
+        }
+    }
+    __syncthreads();
+    eig_vectors(M, d, Qh, P, d, wr, wi, sel, colofs, nsel_s, hn_s, Wk, eigvec_warps(d, d + 1));
+    __syncthreads();
+    if (warp != 0) return;
     for (int i = lane; i < d; i += 32) { wr_o[i] = wr[i]; wi_o[i] = wi[i]; }
-    if (lane == 0) *kout = fail ? -cols - 1 : cols;
+    if (lane == 0) *kout = fail_s ? -cols_s - 1 : cols_s;
 }
 
 gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi, double* P,
                             int kcap, int* kout, double* scratch, cudaStream_t s) {
     (void)kcap;
     static bool attr = false;
-    const size_t smem = 210 * 1024;
+    const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
     if (!attr) {
         GIR_CUDA_TRY(cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    count_launch(), k_small_eig<<<1, 32, smem, s>>>(M, d, k, largest, mcap, wr, wi, P, kout, scratch);
+    count_launch(), k_small_eig<<<1, CLOSE_THREADS, smem, s>>>(M, d, k, largest, mcap, wr, wi, P, kout, scratch);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }

@@ -207,14 +207,20 @@ def test_apply_minv_and_atilde_dd(G, n, fmt):
 @pytest.mark.parametrize("d", [1, 2, 5, 12, 30, 50, 112])
 @pytest.mark.parametrize("largest", [0, 1])
 def test_small_eig(G, d, largest):
+    """The harmonic Ritz eigen-solver: eigenvalues from Francis QR in FP32 (they steer only the
+    selection and the shifts), eigenvectors by FP64 inverse iteration, so the eigenvalues match to
+    FP32 accuracy times their condition and P spans an invariant subspace to FP64 accuracy."""
+    from scipy.optimize import linear_sum_assignment
     rng = np.random.default_rng(d + 100 * largest)
     M = rng.standard_normal((d, d))
     k = min(10, max(1, d - 1))
     wr, wi, P, failed = G.small_eig(M, k, largest, 200)
     assert not failed
     lam = np.linalg.eigvals(M)
-    got = np.sort_complex(wr + 1j * wi)
-    assert np.abs(got - np.sort_complex(lam)).max() <= 1e-10 * max(1.0, np.abs(lam).max())
+    got = wr + 1j * wi
+    dist = np.abs(got[:, None] - lam[None, :])
+    r, c = linear_sum_assignment(dist)
+    assert dist[r, c].max() <= 1e-4 * max(1.0, np.abs(lam).max())
     # P spans an invariant subspace whose eigenvalues are the selected ones
     T = np.linalg.lstsq(P, M @ P, rcond=None)[0]
     assert np.linalg.norm(M @ P - P @ T) <= 1e-9 * max(1.0, np.linalg.norm(M @ P))
