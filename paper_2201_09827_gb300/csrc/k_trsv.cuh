@@ -15,6 +15,8 @@ struct TrsvState {
     int64_t ldl = 0;
     float2* DL = nullptr;            // inverses of the unit-lower diagonal blocks (float-float)
     float2* DU = nullptr;            // inverses of the upper diagonal blocks
+    float2* EL = nullptr;            // DL[I] L[I, I-1] (float-float), the last step of the L solve
+    float2* EU = nullptr;            // DU[I] U[I, I+1], the last step of the U solve
     int* perm = nullptr;             // row permutation P (from the interchanges)
     double* z = nullptr;             // scaled/permuted input (FP64)
     float2* y1 = nullptr;            // intermediate and final solutions (float-float)
@@ -25,6 +27,7 @@ struct TrsvState {
     unsigned long long tickets = 0;  // host mirror of the ticket counter
     int epoch = 0;
     int calls = 0;
+    int cluster = 16;                // CTAs per cluster of the forward solves (16, or 8 where 16 cannot run)
 };
 
 gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, cudaStream_t s);
