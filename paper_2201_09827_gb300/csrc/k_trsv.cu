@@ -329,6 +329,7 @@ __global__ void k_minv_post_t(const float2* __restrict__ y, const int* __restric
 // global memory only once per cluster.
 constexpr int TF_STAGES = 4;
 constexpr int TF_AHEAD = TF_STAGES - 1;
+constexpr size_t TF_DYN_SMEM = (size_t)TF_STAGES * (2 * 256 * 16 + 64 * 8);
 constexpr int TF_MAXCL = 16;
 constexpr long long TF_WAIT_LIMIT = 20000000LL;   // polls of one in-cluster dependency
 
@@ -395,8 +396,11 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
                                                   float2* __restrict__ yout, unsigned long long* __restrict__ ticket_ctr,
                                                   unsigned long long base, int* __restrict__ abort_flag,
                                                   int* __restrict__ flags) {
-    __shared__ __align__(16) uint4 ring[TF_STAGES][2][256];   // [stage][chunk][thread]
-    __shared__ __align__(16) unsigned long long ring_y[TF_STAGES][TB];       // y blocks fetched ahead
+    // dynamic: the ring of tiles [stage][chunk][thread] and the y blocks fetched ahead [stage][TB]
+    extern __shared__ __align__(16) unsigned char tf_dyn[];
+    uint4 (*ring)[2][256] = reinterpret_cast<uint4 (*)[2][256]>(tf_dyn);
+    unsigned long long (*ring_y)[TB] =
+        reinterpret_cast<unsigned long long (*)[TB]>(tf_dyn + (size_t)TF_STAGES * 2 * 256 * sizeof(uint4));
     __shared__ float2 yj[2][TB + 2];                          // padded by one entry per 32
     __shared__ float2 accs[TB + 2];
     __shared__ __align__(8) unsigned long long cbar[TF_MAXCL];               // one per lower rank
@@ -638,6 +642,8 @@ gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n,
     st.ldl = ldl;
     const int smem = 2 * TB * (TB + 1) * (int)sizeof(double);
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TF_DYN_SMEM));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TF_DYN_SMEM));
     if (st.cluster > 8) {
         // 16-CTA clusters are a non-portable size: use them only where the device can hold one
         int ok = 1;
@@ -650,6 +656,7 @@ gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n,
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)st.cluster, 1, 1);
             cfg.blockDim = dim3(256, 1, 1);
+            cfg.dynamicSmemBytes = TF_DYN_SMEM;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = (unsigned)st.cluster;
@@ -702,7 +709,7 @@ static gir_status run_trsv_fwd(TrsvState& st, const float2* D, const float2* E, 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclu * csize), 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = TF_DYN_SMEM;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
