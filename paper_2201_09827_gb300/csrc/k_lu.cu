@@ -1388,8 +1388,17 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
         int t_ = trace_begin(s);
         GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, perm, s));
         GIR_TRY(permute_rows<float>(W, ldw, Cend, n, sw, s));
-        GIR_TRY(permute_rows<uint16_t>(LU, ldl, 0, C0, sw, s));
         trace_end(t_, "lu outer swaps", s);
+        if (C0 > 0) {
+            // the earlier blocks' L columns take the interchanges on the side stream: nothing on the
+            // critical path reads them, and the side stream runs them after the previous block's
+            // (b) part, which reads those rows; the next block's plan waits for ev_b
+            GIR_CUDA_TRY(cudaEventRecord(ev_swapped, s));
+            GIR_CUDA_TRY(cudaStreamWaitEvent(s2, ev_swapped, 0));
+            GIR_TRY(permute_rows<uint16_t>(LU, ldl, 0, C0, sw, s2));
+            GIR_CUDA_TRY(cudaEventRecord(ev_b, s2));
+            b_pending = true;
+        }
         if (Cend < n) {
             const int64_t ntr = n - Cend;
             const int64_t Ca = gmin<int64_t>(n, Cend + NB);  // (a): columns [Cend, Ca)

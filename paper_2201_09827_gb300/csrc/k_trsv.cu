@@ -64,13 +64,13 @@ __global__ void __launch_bounds__(TB) k_diag_inv(const uint16_t* __restrict__ LU
 }
 
 // E[I] = D[I] T_{I,J} with J = I - 1 (L, upper == 0) or I + 1 (U, upper == 1): the product of the
-// diagonal-block inverse with the block the forward solve meets last. FP64 dot products of the
-// float-float D with the u_f tile, stored as float-float (row-major b x b per block); blocks
-// without such a neighbour, and rows/columns beyond n, are zero.
+// diagonal-block inverse with the block the forward solve meets last. Float-float dot products of
+// the float-float D with the u_f tile (exact in FP32), stored as float-float (row-major b x b per
+// block); blocks without such a neighbour, and rows/columns beyond n, are zero.
 __global__ void __launch_bounds__(256) k_diag_e(const uint16_t* __restrict__ LU, int64_t ldl, int64_t n, int fmt,
                                                 int upper, const float2* __restrict__ D, int nblk,
                                                 float2* __restrict__ E) {
-    __shared__ double Ds[TB][TB + 1];
+    __shared__ float2 Ds[TB][TB + 1];
     __shared__ uint16_t Ts[TB][TB + 2];
     const int I = blockIdx.x;
     const int J = upper ? I + 1 : I - 1;
@@ -82,20 +82,21 @@ __global__ void __launch_bounds__(256) k_diag_e(const uint16_t* __restrict__ LU,
     }
     for (int e = tid; e < TB * TB; e += 256) {
         const int i = e / TB, c = e % TB;
-        const float2 d = D[(int64_t)I * TB * TB + e];
-        Ds[i][c] = (double)d.x + (double)d.y;
+        Ds[i][c] = D[(int64_t)I * TB * TB + e];
         const int64_t gi = (int64_t)I * TB + i, gc = (int64_t)J * TB + c;
         Ts[i][c] = (gi < n && gc < n) ? LU[gi * ldl + gc] : (uint16_t)0;   // 0 is +0 in both formats
     }
     __syncthreads();
     const int r = tid >> 2, q = tid & 3;
     for (int c = q * 16; c < q * 16 + 16; ++c) {
-        double s = 0.0;
-        for (int k = 0; k < TB; ++k) s = fma(Ds[r][k], (double)uf_to_float(Ts[k][c], fmt), s);
-        const float h = __double2float_rn(s);
-        const float l = __double2float_rn(s - (double)h);
+        float sh = 0.0f, sl = 0.0f;
+        for (int k = 0; k < TB; ++k) {
+            const float2 d = Ds[r][k];
+            ff_acc_prod1(sh, sl, uf_to_float(Ts[k][c], fmt), d.x, d.y);
+        }
+        const ff v = ff_norm(sh, sl);
         const bool live = (int64_t)I * TB + r < n && (int64_t)J * TB + c < n;
-        Eb[r * TB + c] = live ? make_float2(h, l) : make_float2(0.0f, 0.0f);
+        Eb[r * TB + c] = live ? make_float2(v.h, v.l) : make_float2(0.0f, 0.0f);
     }
 }
 
