@@ -244,6 +244,7 @@ def main():
 
     import torch
     import paper_2201_09827_gb300 as gir
+    from paper_2201_09827_gb300.shard import max_over_ranks
     from synth import randsvd_torch
 
     torch.cuda.set_device(local)
@@ -303,11 +304,7 @@ def main():
     # correctness of the timed result: backward error from a double-double residual
     r = gir.residual(A, x, b, "dd")
     eta = (r.abs().max() / (A.abs().sum(1).max() * x.abs().max() + b.abs().max())).item()
-    ms = statistics.median(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(statistics.median(times), device=dev)
 
     # ---------------- end to end through the public API with host buffers ----------------
     # gir.solve with pinned CPU tensors: H2D of A and b, factor + solve, D2H of x, per step

@@ -499,3 +499,19 @@ def test_bounded_wait_times_out_and_context_survives(pkg):
     b = rhs_uniform(128, 1)
     x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 20, 4, 1e-8, target=1e-15)
     assert info.status == gir.GIR_OK
+
+
+def test_sharded_batch_single_rank(pkg):
+    """The multi-GPU batch path on one rank: sharded_batch_solve runs the whole batch through the
+    CUDA batch solve and returns every system's result in input order."""
+    from paper_2201_09827_gb300 import gir
+    from paper_2201_09827_gb300.shard import sharded_batch_solve
+    sizes = [300, 129, 64]
+    As = [randsvd(n, 1e3, seed=n) for n in sizes]
+    bs = [rhs_uniform(n, 1) for n in sizes]
+    prm = pkg.Params(uf="bf16", m=30, k=8)
+    xs, infos, owner = sharded_batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    assert owner == [0, 0, 0]
+    for x, info, A, b in zip(xs, infos, As, bs):
+        assert info.status == gir.GIR_OK
+        assert normwise_berr(A, x.numpy(), b) <= 2 * UNIT_ROUNDOFF["fp64"]
