@@ -273,6 +273,9 @@ gir_status gir_gemv_t_noalloc(const double* A, int64_t n, int64_t lda, const dou
  * gir_launch_count returns the number of kernels this library has launched so far. */
 void gir_trace_enable(int on);
 int gir_trace_report(char* buf, int buflen);
+/* Restrict the timing to the phases named in a comma-separated list (NULL or "": all phases).
+ * Unselected phases record no events, so their launches run back to back as without timing. */
+void gir_trace_select(const char* names);
 unsigned long long gir_launch_count(void);
 
 #ifdef __cplusplus

@@ -311,13 +311,13 @@ gir_status arnoldi_step(gir_handle* h, const double* A, int64_t lda, int trans, 
     const int64_t n = h->n;
     double* vj = V(h, j);
     double* w = V(h, j + 1);
-    { int tslot_ = trace_begin(s);
+    { int tslot_ = trace_begin(s, "gemv");
     GIR_TRY(launch_op_gemv(h, A, lda, vj, h->vtmp, trans, s));
     trace_end(tslot_, "gemv", s); }
-    { int tslot_ = trace_begin(s);
+    { int tslot_ = trace_begin(s, "minv");
     GIR_TRY(apply_minv_op(h, w, trans, s));
     trace_end(tslot_, "minv", s); }
-    { int tslot_ = trace_begin(s);
+    { int tslot_ = trace_begin(s, "cgs2+givens");
     double* basis = Cregion(h, kc);
     const int p = kc + j + 1;
     GIR_TRY(launch_gemm_tn(basis, h->ldb, p, w, h->ldb, 1, n, ST_PTR(h, s1), p, h->scratch, s));
@@ -341,7 +341,7 @@ gir_status run_cycle(gir_handle* h, const double* A, int64_t lda, int trans, int
     int j = 0;
     for (; j < steps; ++j) {
         GIR_TRY(arnoldi_step(h, A, lda, trans, j, kc, s));
-        { int tslot_ = trace_begin(s);
+        { int tslot_ = trace_begin(s, "step sync");
         GIR_TRY(read_header(h, s));
         trace_end(tslot_, "step sync", s); }
         if (h->hst->status) break;
@@ -425,7 +425,7 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
                 count_launch(), k_set_ktarget<<<1, 32, 0, s>>>(h->st, k);
             }
         }
-        { int tslot_ = trace_begin(s);
+        { int tslot_ = trace_begin(s, "cycle close");
         GIR_TRY(launch_cycle_close(h->st, h->qh, s));
         trace_end(tslot_, "cycle close", s); }
         GIR_TRY(launch_gemm_nn(V(h, 0), h->ldb, j, ST_PTR(h, ycoef), j, 1, d, n, 1.0, 0.0, n, r32, s));
@@ -455,7 +455,7 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
                                    h->scratch, s));
             GIR_TRY(launch_gemm_tn(h->Ucur, n, kc, h->Ucur, n, kc, n, ST_PTR(h, UtU), kc, h->scratch, s));
         }
-        { int tslot_ = trace_begin(s);
+        { int tslot_ = trace_begin(s, "cycle close");
         GIR_TRY(launch_cycle_close(h->st, h->qh, s));
         trace_end(tslot_, "cycle close", s); }
         const int d_dim = kc + j;
@@ -537,7 +537,7 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
     const bool sir = (h->p.flags & GIR_FLAG_SIR) != 0;
     for (int i = 0; i <= imax; ++i) {
         // r_i = b - A x_i in u_r (line 4), stored in u
-        { int tslot_ = trace_begin(s);
+        { int tslot_ = trace_begin(s, "residual");
         if (!trans) {
             GIR_TRY(launch_residual(A, n, lda, x, b, h->rr, h->p.ur == GIR_DD, s, cw ? h->dsc + SC_OMEGA : nullptr));
         } else {

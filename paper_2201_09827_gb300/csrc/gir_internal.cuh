@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "../../include/gir.h"
 
 #define GIR_CUDA_TRY(expr)                                                        \
@@ -26,6 +28,18 @@
     } while (0)
 
 namespace gir {
+
+// Raises a kernel's dynamic shared-memory limit once per device. Safe from several host threads
+// (the batch solve's workers): a race only repeats the idempotent call.
+inline cudaError_t ensure_dyn_smem(const void* fn, int bytes, std::atomic<unsigned>& done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned bit = 1u << (dev & 31);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // Host-side count of kernel launches made by this library (all streams, all handles).
 void count_launch();

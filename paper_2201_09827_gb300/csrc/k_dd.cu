@@ -403,7 +403,7 @@ static gir_status run_trsv_dd(DdState& dd, TrsvState& st, const double2* D, cons
     const unsigned long long base = st.tickets;
     st.tickets += (unsigned long long)dd.nblk;
     const int epoch = ++dd.epoch;
-    const int tslot = trace_begin(s);
+    const int tslot = trace_begin(s, "trsv dd");
     count_launch(), k_trsv_dd<LOWER, TRANS><<<dd.nblk, DT, dd.solo_smem, s>>>(st.LU, st.ldl, st.fmt, D, st.n, dd.nblk, z, y,
                                                                    dd.ready, epoch, st.ticket_ctr, base,
                                                                    st.abort_flag, flags, SPIN_LIMIT);

@@ -262,12 +262,8 @@ gir_status launch_tc_gemm_sub(float* C, int64_t ldc, const uint16_t* A, int64_t 
     CUtensorMap ma, mb;
     if (!encode_map(&ma, A, M, K, lda, tc::BM, fmt) || !encode_map(&mb, Bt, N, K, ldbt, tc::BN, fmt))
         return GIR_UNSUPPORTED;
-    static bool attr = false;
-    if (!attr) {
-        GIR_CUDA_TRY(cudaFuncSetAttribute(tc::k_tc_gemm_sub, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)tc::SMEM_BYTES));
-        attr = true;
-    }
+    static std::atomic<unsigned> attr_done{0};
+    GIR_CUDA_TRY(ensure_dyn_smem((const void*)tc::k_tc_gemm_sub, (int)tc::SMEM_BYTES, attr_done));
     dim3 grid((unsigned)((N + tc::BN - 1) / tc::BN), (unsigned)((M + tc::BM - 1) / tc::BM));
     count_launch(), tc::k_tc_gemm_sub<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(ma, mb, C, ldc, (int)M, (int)N, (int)K,
                                                                 tc::make_idesc(fmt == FF_BF16 ? 1 : 0), flags);

@@ -1338,9 +1338,9 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
         const int64_t Cend = C0 + NBc;
         for (int64_t c0 = C0; c0 < Cend; c0 += w) {
             const int wc = (int)gmin<int64_t>(w, Cend - c0);
-            int t_ = trace_begin(s);
+            int t_ = trace_begin(s, "lu panel");
             // GIR_TRACE_DETAIL=1: the panel phase also reported per panel-height class
-            const int td_ = trace_detail() ? trace_begin(s) : -1;
+            const int td_ = trace_detail() ? trace_begin(s, nullptr) : -1;
             {
                 // the panel kernel also stores the u_f panel, applies its interchanges to the
                 // block's later columns of W and earlier columns of LU, and solves for U12
@@ -1361,7 +1361,7 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             GIR_TRY(debug_check("panel", C0, c0, flags, s));
             if (c0 + wc < Cend) {
                 int64_t ncols = Cend - (c0 + wc);
-                t_ = trace_begin(s);
+                t_ = trace_begin(s, "lu inner gemm");
                 if (fp8) {
                     GIR_TRY(gemm_sub_f32(W + (c0 + wc) * ldw + (c0 + wc), ldw, W + (c0 + wc) * ldw + c0, ldw,
                                          W + c0 * ldw + (c0 + wc), ldw, n - (c0 + wc), ncols, wc, s));
@@ -1385,7 +1385,7 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             GIR_CUDA_TRY(cudaStreamWaitEvent(s, ev_b, 0));
             b_pending = false;
         }
-        int t_ = trace_begin(s);
+        int t_ = trace_begin(s, "lu outer swaps");
         GIR_TRY(make_plan(ipiv, C0, Cend, n, sw, perm, s));
         GIR_TRY(permute_rows<float>(W, ldw, Cend, n, sw, s));
         trace_end(t_, "lu outer swaps", s);
@@ -1403,11 +1403,11 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
             const int64_t ntr = n - Cend;
             const int64_t Ca = gmin<int64_t>(n, Cend + NB);  // (a): columns [Cend, Ca)
             // (a) on the main stream: the next block's columns
-            t_ = trace_begin(s);
+            t_ = trace_begin(s, "lu outer trsm");
             trsm_band(C0, NBc, Cend, Ca, true, s);
             trace_end(t_, "lu outer trsm", s);
             GIR_TRY(debug_check("outer trsm a", C0, Cend, flags, s));
-            t_ = trace_begin(s);
+            t_ = trace_begin(s, "lu outer gemm");
             GIR_TRY(gemm_sub(W + Cend * ldw + Cend, ldw, LU + Cend * ldl + C0, ldl, LU + C0 * ldl + Cend, ldl,
                              UT + Cend * ldut, ldut, ntr, Ca - Cend, NBc, fmt, plan, flags, s));
             trace_end(t_, "lu outer gemm", s);
@@ -1415,10 +1415,10 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
                 // (b) on the side stream, after this block's interchanges
                 GIR_CUDA_TRY(cudaEventRecord(ev_swapped, s));
                 GIR_CUDA_TRY(cudaStreamWaitEvent(s2, ev_swapped, 0));
-                int tb = trace_begin(s2);
+                int tb = trace_begin(s2, "lu outer trsm");
                 trsm_band(C0, NBc, Ca, n, false, s2);
                 trace_end(tb, "lu outer trsm", s2);
-                tb = trace_begin(s2);
+                tb = trace_begin(s2, "lu outer gemm");
                 GIR_TRY(gemm_sub(W + Cend * ldw + Ca, ldw, LU + Cend * ldl + C0, ldl, LU + C0 * ldl + Ca, ldl,
                                  UT + Ca * ldut, ldut, ntr, n - Ca, NBc, fmt, plan, flags, s2));
                 trace_end(tb, "lu outer gemm", s2);

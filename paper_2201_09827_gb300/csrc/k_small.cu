@@ -873,12 +873,9 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, d
 }
 
 gir_status launch_cycle_close(SmallState* st, double* qh_scratch, cudaStream_t s) {
-    static bool attr = false;
+    static std::atomic<unsigned> attr_done{0};
     const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
-    if (!attr) {
-        GIR_CUDA_TRY(cudaFuncSetAttribute(k_cycle_close, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_cycle_close, (int)smem, attr_done));
     double* Qh = qh_scratch;
     double* Pbuf = qh_scratch + SM_DMAX * SM_DMAX;
     double* Gq = Pbuf + SM_DMAX * (SM_KMAX + 2);
@@ -984,12 +981,9 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, 
 gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi, double* P,
                             int kcap, int* kout, double* scratch, cudaStream_t s) {
     (void)kcap;
-    static bool attr = false;
+    static std::atomic<unsigned> attr_done{0};
     const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
-    if (!attr) {
-        GIR_CUDA_TRY(cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_small_eig, (int)smem, attr_done));
     count_launch(), k_small_eig<<<1, CLOSE_THREADS, smem, s>>>(M, d, k, largest, mcap, wr, wi, P, kout, scratch);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;

@@ -689,7 +689,7 @@ static gir_status run_trsv(TrsvState& st, const float2* D, const double* z64, co
     st.tickets += (unsigned long long)st.nblk;
     int epoch = ++st.epoch;
     GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
-    const int tslot = trace_begin(s);
+    const int tslot = trace_begin(s, "trsv");
     count_launch(), k_trsv<LOWER, TRANS><<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, st.nblk, z64, zff, y, ready,
                                                  st.ticket_ctr, base, epoch, st.abort_flag, flags);
     trace_end(tslot, "trsv", s);
@@ -706,7 +706,7 @@ static gir_status run_trsv_fwd(TrsvState& st, const float2* D, const float2* E, 
     unsigned long long base = st.tickets;
     st.tickets += (unsigned long long)nclu;   // one ticket per cluster
     GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
-    const int tslot = trace_begin(s);
+    const int tslot = trace_begin(s, "trsv");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclu * csize), 1, 1);
     cfg.blockDim = dim3(256, 1, 1);

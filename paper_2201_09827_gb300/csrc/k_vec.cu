@@ -296,11 +296,8 @@ gir_status launch_gemm_nn(const double* X, int64_t ldx, int p, const double* Cf,
     }
     size_t smem = (size_t)p * q * sizeof(double);
     if (smem > 48 * 1024) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_gemm_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr_set = true;
-        }
+        static std::atomic<unsigned> attr_done{0};
+        GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_gemm_nn, 200 * 1024, attr_done));
         if (smem > 200 * 1024) return GIR_INVALID_ARG;
     }
     int g = (int)gmin<int64_t>((n + 255) / 256, 152 * 8);

@@ -77,9 +77,20 @@ std::mutex g_trace_mu;   // the batch runs solves on several host threads
 
 bool trace_on() { return g_trace.on; }
 
-int trace_begin(cudaStream_t s) {
+// Phase names to time (empty: all). Phases outside the selection record no events, so a run can
+// time a few kernels without the event records between every launch.
+static std::vector<std::string> g_select;
+
+int trace_begin(cudaStream_t s, const char* name) {
     if (!g_trace.on) return -1;
     std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (!g_select.empty()) {
+        if (!name) return -1;   // a phase named only at its end (diagnostic detail)
+        bool hit = false;
+        for (const auto& n : g_select)
+            if (n == name) { hit = true; break; }
+        if (!hit) return -1;
+    }
     cudaEvent_t a = g_trace.next();
     cudaEventRecord(a, s);
     g_trace.slots.push_back({nullptr, a, nullptr});
@@ -136,6 +147,22 @@ int gir_trace_report(char* buf, int buflen) {
         gir::g_trace.agg.clear();  // a size query (buf == NULL) keeps the totals
     }
     return (int)out.size();
+}
+
+void gir_trace_select(const char* names) {
+    std::lock_guard<std::mutex> lk(gir::g_trace_mu);
+    gir::g_select.clear();
+    if (!names) return;
+    std::string cur;
+    for (const char* p = names;; ++p) {
+        if (*p == ',' || *p == 0) {
+            if (!cur.empty()) gir::g_select.push_back(cur);
+            cur.clear();
+            if (*p == 0) break;
+        } else {
+            cur += *p;
+        }
+    }
 }
 
 unsigned long long gir_launch_count(void) { return gir::g_launches.load(); }

@@ -4,7 +4,7 @@
 
 namespace gir {
 bool trace_on();
-int trace_begin(cudaStream_t s);
+int trace_begin(cudaStream_t s, const char* name);
 void trace_end(int slot, const char* name, cudaStream_t s);
 // GIR_TRACE_DETAIL=1 (with tracing on): extra per-class phases for diagnosis
 bool trace_detail();

@@ -74,6 +74,7 @@ SYMBOLS = {
     "gir_gemv_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gir_trace_enable": (None, [C.c_int]),
     "gir_trace_report": (C.c_int, [C.c_char_p, C.c_int]),
+    "gir_trace_select": (None, [C.c_char_p]),
     "gir_launch_count": (C.c_ulonglong, []),
     "gir_small_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_int, C.POINTER(C.c_int)]),
@@ -373,6 +374,11 @@ def lu_update(Cm: torch.Tensor, A16: torch.Tensor, B16: torch.Tensor, fmt="bf16"
 
 def trace_enable(on=True):
     load().gir_trace_enable(int(on))
+
+
+def trace_select(names=None):
+    """Time only the named phases (None: all)."""
+    load().gir_trace_select(None if not names else ",".join(names).encode())
 
 
 def trace_report():
