@@ -15,7 +15,7 @@ The steps follow Algorithm 3 in its order:
   G^T G z = theta G^T W^T V^ z with the k smallest |theta| give P_k;
   QR(G P_k) = QR, C = W^ Q, U = V^ P_k R^-1.
 
-Readings where the paper is silent or garbled (each listed in the design doc):
+Readings where the paper is silent or garbled:
 * "||r|| > tau": tau is relative to ||c|| (= ||r0||, d0 = 0), Section 4's "relative
   (preconditioned) residual norm drops below tau".
 * Arnoldi stops early inside a cycle when the Givens residual estimate drops below the

@@ -11,7 +11,7 @@ RGMRES-IR, Algorithm 4, in order:
      x_{i+1} = fl_u(x_i + s d).
   GMRES-IR (Algorithm 2) is the same loop with k = 0 (GCRO-DR(m, 0) is restarted GMRES(m)).
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here:
 * "converged": eta_i <= target (normwise relative backward error); with ``stop='cw'`` also
   omega_i <= target (componentwise backward error, the middle column of Table 2); or, with
   ``stop='all'`` and a known exact solution, max(normwise BE, componentwise BE,

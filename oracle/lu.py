@@ -14,8 +14,8 @@ operands L21 and U12 rounded to u_f with exact products and FP32-or-better
 accumulation. The stored factors are the u_f-rounded values. For fp16 the matrix is
 first equilibrated by powers of two and scaled by mu (diagonal scaling against
 overflow); for fp8-e4m3 each 128 x 128 tile of an operand gets its own power-of-two
-scale. These are readings of "LU in precision u_f" for hardware formats, listed in
-the design doc; ``lu_block`` with fmt='fp64' is plain GEPP and is pinned against LAPACK.
+scale. These are readings of "LU in precision u_f" for hardware formats;
+``lu_block`` with fmt='fp64' is plain GEPP and is pinned against LAPACK.
 
 The factors define M^-1 = mu S U^-1 L^-1 P R, the left preconditioner of the
 correction equation (Algorithm 4, line 5); ``apply_minv`` applies it in a chosen

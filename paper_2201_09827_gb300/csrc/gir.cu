@@ -109,7 +109,7 @@ gir_status dalloc_t(T** p, size_t count) {
 
 // Handles and factorization temporaries come from the device's stream-ordered pool, which is
 // told to keep freed memory (release threshold = max) so that repeated factorizations reuse
-// it without going back to the driver.
+// it without new allocations from the CUDA driver.
 gir_status pool_alloc(void** p, size_t bytes, cudaStream_t s) {
     static std::atomic<int> configured_dev{-1};
     int dev = 0;
