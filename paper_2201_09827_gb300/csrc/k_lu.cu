@@ -843,6 +843,8 @@ __global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, in
                                                    int64_t ldw, int64_t r0, int nb, int64_t col0, int64_t col1,
                                                    int fmt, uint16_t* __restrict__ UT, int64_t ldut) {
     constexpr int XS = TBC + 1;
+    constexpr int CPW = TBC / 8;                // columns per warp in the diagonal block
+    static_assert(TBC % 8 == 0, "the diagonal block's columns are spread over 8 warps");
     constexpr int CG = TBC / 4;                 // column groups of 4 in the update
     constexpr int RG = 256 / CG;                // row groups
     constexpr int MAXR = (TB_MAXNB - 32 + RG - 1) / RG;
@@ -881,25 +883,36 @@ __global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, in
         const uint16_t* L = Lb + (step & 1) * TB_MAXNB * TB_LS;
         const bool more = b0 + 32 < nb;
         if (more) fetch(b0 + 32);
-        if (tid < TBC) {
-            // forward substitution in the diagonal block, one thread per column
-            const int c = tid;
-            float x[32];
+        {
+            // forward substitution in the diagonal block: lane i of a warp holds row b0 + i (its
+            // 32 multipliers in registers) for the warp's columns wp, wp + 8, ...; at step q lane q
+            // holds the final x_q, which the lanes below take by shuffle: row i gets
+            // x_i - L_i0 x_0 - L_i1 x_1 - ... by FMAs in ascending q, one dependent FMA per step
+            const int lane = tid & 31, wp = tid >> 5;
+            uint32_t lr[16];   // L[b0 + lane][0..31] as u16 pairs (zero on and above the diagonal)
+            const uint32_t* Lrow = reinterpret_cast<const uint32_t*>(L + (b0 + lane) * TB_LS);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = (i < wb) ? X[(b0 + i) * XS + c] : 0.0f;
+            for (int k = 0; k < 16; ++k) lr[k] = (lane < wb) ? Lrow[k] : 0u;
+            float x[CPW];
 #pragma unroll
-            for (int i = 1; i < 32; ++i) {
-                float acc = x[i];
+            for (int j = 0; j < CPW; ++j) x[j] = (lane < wb) ? X[(b0 + lane) * XS + wp + 8 * j] : 0.0f;
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    if (q < i) acc = fmaf(-uf_to_float(L[(b0 + i) * TB_LS + q], fmt), x[q], acc);
-                x[i] = acc;
+            for (int q = 0; q < 31; ++q) {
+                const uint32_t pair = lr[q >> 1];
+                const float lq = uf_to_float((uint16_t)((q & 1) ? (pair >> 16) : (pair & 0xffffu)), fmt);
+#pragma unroll
+                for (int j = 0; j < CPW; ++j) {
+                    const float xq = __shfl_sync(0xffffffffu, x[j], q);
+                    if (lane > q) x[j] = fmaf(-lq, xq, x[j]);
+                }
             }
+            if (lane < wb) {
+                const int i = lane;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (i < wb) {
+                for (int j = 0; j < CPW; ++j) {
+                    const int c = wp + 8 * j;
                     if (RND) {
-                        const uint16_t u = float_to_uf(x[i], fmt);
+                        const uint16_t u = float_to_uf(x[j], fmt);
                         const float uv = uf_to_float(u, fmt);
                         X[(b0 + i) * XS + c] = uv;
                         if (c < width) {
@@ -909,8 +922,8 @@ __global__ void __launch_bounds__(256) k_trsm_band(uint16_t* __restrict__ LU, in
                         }
                     } else {
                         // FP8 blocks: FP32 values throughout, rounded tile by tile afterwards
-                        X[(b0 + i) * XS + c] = x[i];
-                        if (c < width) W[(r0 + b0 + i) * ldw + c0 + c] = x[i];
+                        X[(b0 + i) * XS + c] = x[j];
+                        if (c < width) W[(r0 + b0 + i) * ldw + c0 + c] = x[j];
                     }
                 }
             }
@@ -1228,12 +1241,12 @@ gir_status lu_prepare(LUPlan& plan) {
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)trsm_band_smem<16>()));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_band_smem<8>()));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)trsm_band_smem<64>()));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)trsm_band_smem<16>()));
+    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_band_smem<8>()));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsm_band<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)trsm_band_smem<64>()));
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_swap_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1312,15 +1325,15 @@ gir_status lu_factor(float* W, int64_t ldw, uint16_t* LU, int64_t ldl, int* ipiv
     bool b_pending = false;  // a (b) part is running on s2
     gir_status st = GIR_OK;
     // wide column slabs for the bulk (two CTAs per SM), narrow ones for the next block's 256
-    // columns on the critical path (16 CTAs)
+    // columns on the critical path (32 CTAs of 8 columns: the solve is latency-bound there)
     auto trsm_band = [&](int64_t C0, int64_t NBc, int64_t col0, int64_t col1, bool narrow, cudaStream_t ss) {
         if (col1 <= col0) return;
         if (narrow) {
             if (fp8)
-                count_launch(), k_trsm_band<16, false><<<(unsigned)((col1 - col0 + 15) / 16), 256, trsm_band_smem<16>(), ss>>>(
+                count_launch(), k_trsm_band<8, false><<<(unsigned)((col1 - col0 + 7) / 8), 256, trsm_band_smem<8>(), ss>>>(
                     LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
             else
-                count_launch(), k_trsm_band<16, true><<<(unsigned)((col1 - col0 + 15) / 16), 256, trsm_band_smem<16>(), ss>>>(
+                count_launch(), k_trsm_band<8, true><<<(unsigned)((col1 - col0 + 7) / 8), 256, trsm_band_smem<8>(), ss>>>(
                     LU, ldl, W, ldw, C0, (int)NBc, col0, col1, fmt, UT, ldut);
         } else {
             if (fp8)
