@@ -200,8 +200,12 @@ gir_status launch_gemv(const double* A, int64_t n, int64_t lda, const double* v,
 }
 
 // ------------------------------------------------------------------ tall-skinny X^T Y
-// G[c + t*p] = sum_i X[i, c] Y[i, t]; block = row chunk of TS_CHUNK rows, one warp per (c, t) pair.
+// G[c + t*p] = sum_i X[i, c] Y[i, t]. Block (b, g) covers rows [b TS_CHUNK, (b+1) TS_CHUNK) for
+// the pairs (c, t) with index 8 g .. 8 g + 7, one warp per pair: the FP64 products (one warp
+// instruction per 64 cycles of an SM sub-partition on this GPU) spread over every SM rather
+// than over one CTA per row chunk. Partial sums per chunk go to part[b * pairs + pair].
 constexpr int TS_CHUNK = 1024;
+constexpr int TS_PAIRS = 8;   // pairs per CTA (one per warp)
 
 __global__ void __launch_bounds__(256) k_gemm_tn_partial(const double* __restrict__ X, int64_t ldx, int p,
                                                          const double* __restrict__ Y, int64_t ldy, int q,
@@ -210,15 +214,16 @@ __global__ void __launch_bounds__(256) k_gemm_tn_partial(const double* __restric
     const int64_t i0 = (int64_t)blockIdx.x * TS_CHUNK;
     const int64_t i1 = min(n, i0 + TS_CHUNK);
     const int pairs = p * q;
-    for (int pq = warp; pq < pairs; pq += 8) {
-        int c = pq % p, t = pq / p;
-        const double* xc = X + (int64_t)c * ldx;
-        const double* yt = Y + (int64_t)t * ldy;
-        double acc = 0.0;
-        for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(xc[i], yt[i], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) part[(int64_t)blockIdx.x * pairs + pq] = acc;
-    }
+    const int pq = (int)blockIdx.y * TS_PAIRS + warp;
+    if (pq >= pairs) return;   // the warp's pair does not exist (no CTA barrier follows)
+    const int c = pq % p, t = pq / p;
+    const double* xc = X + (int64_t)c * ldx;
+    const double* yt = Y + (int64_t)t * ldy;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(xc[i], yt[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) part[(int64_t)blockIdx.x * pairs + pq] = acc;
 }
 
 __global__ void k_sum_parts(const double* __restrict__ part, int nparts, int p, int cnt, int ldg,
@@ -235,8 +240,9 @@ gir_status launch_gemm_tn(const double* X, int64_t ldx, int p, const double* Y, 
     if (p <= 0 || q <= 0) return GIR_OK;
     int nb = (int)((n + TS_CHUNK - 1) / TS_CHUNK);
     if (nb < 1) nb = 1;
-    count_launch(), k_gemm_tn_partial<<<nb, 256, 0, s>>>(X, ldx, p, Y, ldy, q, n, scratch);
     int cnt = p * q;
+    const dim3 grid((unsigned)nb, (unsigned)((cnt + TS_PAIRS - 1) / TS_PAIRS), 1);
+    count_launch(), k_gemm_tn_partial<<<grid, 256, 0, s>>>(X, ldx, p, Y, ldy, q, n, scratch);
     count_launch(), k_sum_parts<<<(cnt + 127) / 128, 128, 0, s>>>(scratch, nb, p, cnt, ldg, G);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
@@ -248,8 +254,11 @@ gir_status launch_multidot(const double* X, int64_t ldx, int ncols, const double
 }
 
 // ------------------------------------------------------------------ Y = beta Y + X Cf
-// Thread per row; coefficients staged in shared memory; outputs in groups of 8 columns.
-__global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, int64_t ldx, int p,
+// Thread per row (128-thread CTAs, so that the rows of n = 16384 reach 128 SMs); coefficients
+// staged in shared memory; outputs in groups of 8 columns. Each row's sum runs over c in order;
+// the loads of 8 columns are issued ahead of their products.
+constexpr int NN_THREADS = 128;
+__global__ void __launch_bounds__(NN_THREADS) k_gemm_nn(const double* __restrict__ X, int64_t ldx, int p,
                                                  const double* __restrict__ Cf, int ldc, int q,
                                                  double* __restrict__ Y, int64_t ldy, double alpha, double beta,
                                                  int64_t n, int round32) {
@@ -264,8 +273,19 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, i
             double acc[8];
 #pragma unroll
             for (int tt = 0; tt < 8; ++tt) acc[tt] = 0.0;
-            for (int c = 0; c < p; ++c) {
-                double xv = X[i + (int64_t)c * ldx];
+            int c = 0;
+            for (; c + 8 <= p; c += 8) {
+                double xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xv[u] = X[i + (int64_t)(c + u) * ldx];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int tt = 0; tt < 8; ++tt)
+                        if (t0 + tt < q) acc[tt] = fma(xv[u], sc[c + u + (t0 + tt) * p], acc[tt]);
+            }
+            for (; c < p; ++c) {
+                const double xv = X[i + (int64_t)c * ldx];
 #pragma unroll
                 for (int tt = 0; tt < 8; ++tt)
                     if (t0 + tt < q) acc[tt] = fma(xv, sc[c + (t0 + tt) * p], acc[tt]);
@@ -300,8 +320,8 @@ gir_status launch_gemm_nn(const double* X, int64_t ldx, int p, const double* Cf,
         GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_gemm_nn, 200 * 1024, attr_done));
         if (smem > 200 * 1024) return GIR_INVALID_ARG;
     }
-    int g = (int)gmin<int64_t>((n + 255) / 256, 152 * 8);
-    count_launch(), k_gemm_nn<<<g, 256, smem, s>>>(X, ldx, p, Cf, ldc, q, Y, ldy, alpha, beta, n, round32);
+    int g = (int)gmin<int64_t>((n + NN_THREADS - 1) / NN_THREADS, 152 * 16);
+    count_launch(), k_gemm_nn<<<g, NN_THREADS, smem, s>>>(X, ldx, p, Cf, ldc, q, Y, ldy, alpha, beta, n, round32);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
