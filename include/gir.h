@@ -66,7 +66,7 @@ typedef struct {
     int imax;           /* maximum number of refinement steps */
     double target_berr; /* stop when ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= target_berr;
                            a negative value selects 2*u; 0 runs exactly imax steps */
-    int carry_mode;     /* 0: recompute QR(A~ Y~) at each new refinement step (Algorithm 3, lines 1-4);
+    int carry_mode;     /* 0: recompute QR(A~ Y~) at each new refinement step (the start of Algorithm 3);
                            1: reuse (U_k, C_k), which satisfy A~ U_k = C_k already */
     int max_its;        /* cap on Arnoldi steps per GCRO-DR call (<= 0: 20*m) */
     int lu_nb;          /* LU outer block width (<= 0: the tuned value for this size class, if
@@ -91,6 +91,12 @@ typedef struct {
  * GIR_MAX_K) -- the whole first-step subspace is recycled -- for that cycle's extraction and every
  * later step and solve. If that cycle does not converge, params.k stays. info.k_eff reports it. */
 #define GIR_FLAG_ADAPTIVE_K 0x8u
+/* Harmonic Ritz eigenvalues (Algorithm 3, the eigenproblems at the end of each cycle) by FP64
+ * Hessenberg QR instead of the default FP32 one. The eigenvalues decide which k eigenvectors are
+ * recycled and seed the FP64 inverse iteration that computes them; FP32 is enough unless
+ * |theta| values within about 1e-6 relative of each other straddle the k-th place. The FP64
+ * iteration takes several times longer on GB300 (its dependent FP64 chains). */
+#define GIR_FLAG_EIG_FP64 0x10u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64
@@ -114,15 +120,15 @@ typedef struct {
 
 typedef struct gir_handle gir_handle;
 
-/* Algorithm 4, line 1: factor P (mu R A S) = L U in precision u_f with partial pivoting.
+/* Algorithm 4, the factorization step: factor P (mu R A S) = L U in precision u_f with partial pivoting.
  * A: device, n x n row-major, lda >= n; read only, not retained.
  * Allocates the handle (factors, pivots, scalings, recycle space, workspaces); *out owns it.
  * Returns GIR_SINGULAR on a zero pivot, GIR_NONFINITE on overflow, GIR_OOM. Synchronises. */
 gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params* params,
                       void* stream, gir_handle** out);
 
-/* Algorithm 4, lines 2-8: x0 = M^-1 b, then refinement steps with GCRO-DR corrections.
- * A: the same FP64 matrix that was factored (needed for the residual in u_r, line 4).
+/* Algorithm 4 after the factorization: x0 = M^-1 b, then refinement steps with GCRO-DR corrections.
+ * A: the same FP64 matrix that was factored (needed for the residual in u_r).
  * b: device n-vector; x: device n-vector (output). info: host struct (may be NULL).
  * The recycle space persists in the handle: later calls with new b start from it (Section 2).
  * Returns GIR_OK, GIR_NOT_CONVERGED (x holds the last iterate), GIR_NONFINITE, GIR_TIMEOUT. */
@@ -172,12 +178,12 @@ int64_t gir_handle_n(const gir_handle* h);
 
 /* ----- single steps of the hot path, exposed for parity testing and benchmarking ----- */
 
-/* Line 4 of Algorithm 4: r = b - A x in precision prec (GIR_FP64 or GIR_DD), rounded to FP64.
+/* The residual of Algorithm 4: r = b - A x in precision prec (GIR_FP64 or GIR_DD), rounded to FP64.
  * All device pointers; r must not alias x or b. */
 gir_status gir_residual(const double* A, int64_t n, int64_t lda, const double* x, const double* b,
                         double* r, gir_prec prec, void* stream);
 
-/* Backward errors of an approximate solution x (the stop test of Algorithm 4, line 7, and the
+/* Backward errors of an approximate solution x (the stop test of Algorithm 4 and the
  * two backward-error columns of Table 2): with r = b - A x in precision prec (GIR_FP64 or GIR_DD),
  *   *eta   = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf)          (normwise)
  *   *omega = max_i |r_i| / (|A| |x| + |b|)_i, with 0/0 = 0          (componentwise).
@@ -208,7 +214,7 @@ gir_status gir_export_factors(const gir_handle* h, float* LU, int32_t* ipiv, dou
 gir_status gir_apply_minv(gir_handle* h, const double* v, double* w, int trans, void* stream);
 
 /* w = M^-1 A v (trans = 0) or M^-T A^T v (trans = 1): one application of the preconditioned
- * operator of Algorithm 4, line 5 (device pointers). */
+ * operator of Algorithm 4's correction equation (device pointers). */
 gir_status gir_apply_atilde(gir_handle* h, const double* A, int64_t lda, const double* v, double* w,
                             int trans, void* stream);
 
@@ -226,16 +232,18 @@ gir_status gir_export_recycle(const gir_handle* h, int adjoint, double* U, doubl
 /* Drop the recycle spaces held by the handle (the next solve starts with a GMRES cycle). */
 gir_status gir_reset_recycle(gir_handle* h);
 
-/* Eigenvalues and selected real eigenbasis of a small dense matrix by the single-block FP64
- * solver used for the harmonic Ritz step (Algorithm 3, lines 9 and 19). M: host d x d
- * column-major (d <= GIR_MAX_M + GIR_MAX_K); wr, wi: host double[d] eigenvalues; P: host
- * d x kcap column-major receiving a real basis of the eigenvectors of the k eigenvalues of
- * largest (largest != 0) or smallest (largest == 0) magnitude with the conjugate-pair rule;
- * *k_out receives the number of columns written. Runs on the GPU; for testing. */
+/* Eigenvalues and selected real eigenbasis of a small dense matrix by the single-block solver
+ * used for the harmonic Ritz step (Algorithm 3, the eigenproblems at the end of each cycle):
+ * FP64 Hessenberg reduction, eigenvalues by Hessenberg QR in eig_prec (GIR_FP32, the solver's
+ * default, or GIR_FP64), eigenvectors by FP64 inverse iteration. M: host d x d column-major
+ * (d <= GIR_MAX_M); wr, wi: host double[d] eigenvalues; P: host d x kcap column-major receiving
+ * a real basis of the eigenvectors of the k eigenvalues of largest (largest != 0) or smallest
+ * (largest == 0) magnitude with the conjugate-pair rule; *k_out receives the number of columns
+ * written (-cols-1 if the QR iteration ran out of steps). Runs on the GPU; for testing. */
 gir_status gir_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi,
-                         double* P, int kcap, int* k_out);
+                         double* P, int kcap, int* k_out, gir_prec eig_prec);
 
-/* GEPP of one panel (Algorithm 4, line 1, the column-by-column pivot search): factor the
+/* GEPP of one panel (Algorithm 4's factorization, the column-by-column pivot search): factor the
  * m x w FP32 block W (device, row-major, leading dimension ldw, w <= 32) in place with
  * partial pivoting in FP32 arithmetic; ipiv (device int[w]) receives the 0-based pivot rows.
  * cluster > 0 forces the number of cooperating CTAs (1..16), 0 chooses it from m.
@@ -256,12 +264,13 @@ gir_status gir_lu_update(float* C, int64_t ldc, const uint16_t* A, int64_t lda, 
  * a hot loop, a real-time loop, a fixed memory budget). The paper has no counterpart: this is
  * gir_gemv(trans = 1) with its scratch of partial sums taken from a fixed array in the
  * library's device image instead of cudaMalloc; the library allocates nothing in this call.
- * Limit: ceil(n / 256) * n <= 524288 scratch doubles, i.e. n <= 11585; larger n returns
+ * Limit: ceil(n / 256) * n <= 524288 scratch doubles, i.e. n <= 11520; larger n returns
  * GIR_INVALID_ARG with a message on stderr. The first call on each device looks up the
  * array's address (cudaGetSymbolAddress) with that device current, so make that first call
  * before any stream capture. All calls share the array: calls whose kernels could overlap on
  * the GPU (other streams, other host threads) race on it. Enqueued on `stream`; returns
- * before the kernels finish. Every GPU that loads the library keeps the 4 MiB array until exit. */
+ * before the kernels finish. Every GPU that loads the library keeps the 4 MiB array until exit.
+ * A cudaDeviceReset invalidates the address looked up at the first call. */
 gir_status gir_gemv_t_noalloc(const double* A, int64_t n, int64_t lda, const double* v, double* w,
                               void* stream);
 

@@ -10,7 +10,7 @@ step by step:
 
 * ``formats``   -- rounding to fp16 / bf16 / fp32 / fp8-e4m3 (unit roundoffs of Table 1).
 * ``dd``        -- double-double arithmetic (stands in for the paper's quad precision).
-* ``lu``        -- LU with partial pivoting in precision u_f (Algorithm 4, line 1), in the
+* ``lu``        -- LU with partial pivoting in precision u_f (Algorithm 4, the factorization step), in the
                    paper's "every operation rounded" form and in the block-FMA form
                    (u_f operands, FP32 accumulation) that tensor cores implement.
 * ``gcrodr``    -- GCRO-DR(m, k) (Algorithm 3) including the harmonic-Ritz recycle update.

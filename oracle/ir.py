@@ -193,7 +193,7 @@ def solve(A, b, p: Params, F=None, xstar=None, transpose=False, Y0=None):
         if i == p.imax:
             break
         if p.solver == "sir":
-            # Algorithm 1, lines 5-6: d = U^-1 L^-1 r by substitution (in u_a, stored in u), x = x + d
+            # Algorithm 1, correction and update: d = U^-1 L^-1 r by substitution (in u_a, stored in u), x = x + d
             x = fu(x + fu(minv(r)))
             info.its.append(0)
             info.carry_applies.append(0)

@@ -18,7 +18,7 @@ scale. These are readings of "LU in precision u_f" for hardware formats;
 ``lu_block`` with fmt='fp64' is plain GEPP and is pinned against LAPACK.
 
 The factors define M^-1 = mu S U^-1 L^-1 P R, the left preconditioner of the
-correction equation (Algorithm 4, line 5); ``apply_minv`` applies it in a chosen
+correction equation (Algorithm 4); ``apply_minv`` applies it in a chosen
 precision and ``apply_minv_t`` applies its transpose (used by the adjoint solve).
 """
 from __future__ import annotations
@@ -327,7 +327,7 @@ def unit_roundoff(fmt):
 
 
 def apply_atilde(A, F: Factors, v, prec="fp64", out_fmt=None):
-    """A~ v = M^-1 (A v): the preconditioned operator of Algorithm 4, line 5, in precision ``prec``.
+    """A~ v = M^-1 (A v): the preconditioned operator of Algorithm 4's correction equation, in precision ``prec``.
 
     For 'dd' the product A v and both substitutions are carried in double-double
     without an intermediate rounding (the paper's u^2 = quad application for u = FP64).

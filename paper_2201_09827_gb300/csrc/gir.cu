@@ -177,7 +177,7 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->k < 0 || p->k >= p->m || p->k > GIR_MAX_K) return GIR_INVALID_ARG;
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
-    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR | GIR_FLAG_ADAPTIVE_K)) != 0)
+    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR | GIR_FLAG_ADAPTIVE_K | GIR_FLAG_EIG_FP64)) != 0)
         return GIR_INVALID_ARG;
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
@@ -216,8 +216,10 @@ __global__ void k_set_ktarget(SmallState* st, int k) {
     if (threadIdx.x == 0) st->k_target = k;
 }
 // Initialise the small state for a new cycle: beta from device memory, tol, counters.
-__global__ void k_cycle_init(SmallState* st, const double* beta, double tol, int kc, int first, int k, int m) {
+__global__ void k_cycle_init(SmallState* st, const double* beta, double tol, int kc, int first, int k, int m,
+                             int eig64) {
     if (threadIdx.x != 0) return;
+    st->eig64 = eig64;
     st->j = 0;
     st->kc = kc;
     st->converged = 0;
@@ -306,7 +308,7 @@ gir_status apply_minv_h(gir_handle* h, const double* v, double* w, int trans, cu
     return apply_minv(h->trsv, v, w, R, S, h->mu, trans, h->round32, h->dflags, s);
 }
 
-// One Arnoldi step j of (I - C C^T) A~ with CGS2 (Algorithm 3, line 15; first cycle line 7).
+// One Arnoldi step j of (I - C C^T) A~ with CGS2 (Algorithm 3: the Arnoldi process of each cycle; plain GMRES in the first).
 gir_status arnoldi_step(gir_handle* h, const double* A, int64_t lda, int trans, int j, int kc, cudaStream_t s) {
     const int64_t n = h->n;
     double* vj = V(h, j);
@@ -337,7 +339,8 @@ gir_status run_cycle(gir_handle* h, const double* A, int64_t lda, int trans, int
     // v_1 = r / ||r||  (||r|| is in dsc[SC_NRM2])
     GIR_CUDA_TRY(cudaMemcpyAsync(V(h, 0), h->r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     GIR_TRY(launch_scale_by(V(h, 0), h->n, h->dsc + SC_NRM2, 1, h->round32, s));
-    count_launch(), k_cycle_init<<<1, 32, 0, s>>>(h->st, h->dsc + SC_NRM2, tol, kc, first, h->k_run, h->p.m);
+    count_launch(), k_cycle_init<<<1, 32, 0, s>>>(h->st, h->dsc + SC_NRM2, tol, kc, first, h->k_run, h->p.m,
+                                                   (h->p.flags & GIR_FLAG_EIG_FP64) ? 1 : 0);
     int j = 0;
     for (; j < steps; ++j) {
         GIR_TRY(arnoldi_step(h, A, lda, trans, j, kc, s));
@@ -485,7 +488,7 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
         GIR_TRY(read_scalars(h, s));
         rn = h->hsc[SC_NRM2];
     }
-    // keep the recycle space for the next system (Algorithm 3, line 23: Y~ = U_k)
+    // keep the recycle space for the next system (Algorithm 3 ends with Y~ = U_k)
     rc.k = (k > 0) ? kc : 0;
     rc.c_valid = rc.k > 0;
     if (rc.k > 0) {
@@ -500,7 +503,7 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
     return GIR_OK;
 }
 
-// Refinement loop of Algorithm 4 (lines 2-8); trans solves the adjoint system.
+// Refinement loop of Algorithm 4 (initial solve, then residual, correction and update); trans solves the adjoint system.
 gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, double* x, gir_info* info, int trans,
                   cudaStream_t s) {
     const int64_t n = h->n;
@@ -509,7 +512,7 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
     const int r32 = h->round32;
     Recycle& rc = trans ? h->adj : h->fwd;
     if (trans && h->adj.k == 0 && h->fwd.k > 0 && h->k_run > 0) {
-        // seed the adjoint recycle space with the forward U_k (any Y~ is a valid start, Algorithm 3 line 2)
+        // seed the adjoint recycle space with the forward U_k (any Y~ is a valid start of Algorithm 3)
         h->adj.k = h->fwd.k;
         GIR_CUDA_TRY(cudaMemcpyAsync(h->adj.U, h->fwd.U, (size_t)h->fwd.k * n * sizeof(double), cudaMemcpyDeviceToDevice,
                                      s));
@@ -525,7 +528,7 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
         h->normA_ptr = A;
     }
     GIR_TRY(launch_norminf(b, n, h->dsc + SC_BINF, s));
-    // x0 = M^-1 b (line 2), stored in u
+    // x0 = M^-1 b (Algorithm 4, initial solve), stored in u
     GIR_TRY(apply_minv_h(h, b, x, trans, s));
     const int imax = h->p.imax;
     double target = h->p.target_berr;
@@ -536,7 +539,7 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
     const bool cw = (h->p.flags & GIR_FLAG_CW_BERR) && !trans;
     const bool sir = (h->p.flags & GIR_FLAG_SIR) != 0;
     for (int i = 0; i <= imax; ++i) {
-        // r_i = b - A x_i in u_r (line 4), stored in u
+        // r_i = b - A x_i in u_r (Algorithm 4, residual), stored in u
         { int tslot_ = trace_begin(s, "residual");
         if (!trans) {
             GIR_TRY(launch_residual(A, n, lda, x, b, h->rr, h->p.ur == GIR_DD, s, cw ? h->dsc + SC_OMEGA : nullptr));
@@ -566,11 +569,11 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
             break;
         }
         if (i == imax) break;
-        // r^ = fl_u(r / ||r||_inf) ; c = M^-1 r^ (line 5 right-hand side)
+        // r^ = fl_u(r / ||r||_inf) ; c = M^-1 r^ (right-hand side of the correction equation)
         GIR_TRY(launch_scale_by(h->rr, n, h->dsc + SC_RINF, 1, r32, s));
         int its = 0, capp = 0, conv = 0;
         if (sir) {
-            // Algorithm 1, line 5: the correction by substitution with the factors, d = M^-1 r^
+            // Algorithm 1: the correction by substitution with the factors, d = M^-1 r^
             GIR_TRY(apply_minv_h(h, h->rr, h->dvec, trans, s));
         } else {
             GIR_TRY(apply_minv_h(h, h->rr, h->cvec, trans, s));
@@ -584,7 +587,7 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
         loc.carry_applies[i] = capp;
         loc.total_its += its;
         loc.ir_steps = i + 1;
-        // x_{i+1} = fl_u(x_i + ||r_i||_inf d) (line 6)
+        // x_{i+1} = fl_u(x_i + ||r_i||_inf d) (Algorithm 4, update)
         count_launch(), k_axpy_dev<<<grid1(n), 256, 0, s>>>(x, h->dvec, h->dsc + SC_RINF, n, r32);
     }
     cudaEventRecord(h->ev1, s);
@@ -972,8 +975,9 @@ gir_status gir_reset_recycle(gir_handle* h) {
 }
 
 gir_status gir_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi, double* P,
-                         int kcap, int* k_out) {
+                         int kcap, int* k_out, gir_prec eig_prec) {
     if (!M || !wr || !wi || !P || !k_out || d < 1 || d > SM_DMAX || k < 0 || k > kcap) return GIR_INVALID_ARG;
+    if (eig_prec != GIR_FP32 && eig_prec != GIR_FP64) return GIR_INVALID_ARG;
     double *dM = nullptr, *dwr = nullptr, *dwi = nullptr, *dP = nullptr, *scr = nullptr;
     int* dk = nullptr;
     gir_status st = GIR_OK;
@@ -987,7 +991,7 @@ gir_status gir_small_eig(const double* M, int d, int k, int largest, int mcap, d
     if (st == GIR_OK) {
         cudaMemcpy(dM, M, (size_t)d * d * sizeof(double), cudaMemcpyHostToDevice);
         cudaMemset(dP, 0, (size_t)d * (kcap + 2) * sizeof(double));
-        st = launch_small_eig(dM, d, k, largest, mcap, dwr, dwi, dP, kcap, dk, scr, 0);
+        st = launch_small_eig(dM, d, k, largest, mcap, eig_prec == GIR_FP64, dwr, dwi, dP, kcap, dk, scr, 0);
         if (st == GIR_OK) {
             if (cudaDeviceSynchronize() != cudaSuccess) st = GIR_CUDA_ERROR;
         }

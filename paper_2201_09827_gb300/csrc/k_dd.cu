@@ -1,5 +1,5 @@
 // The preconditioned operator A~ = M^-1 A applied in double-double (unit roundoff about
-// 2^-106): the paper's u_a = u^2 for the working precision u = FP64 (Algorithm 4, line 5; the
+// 2^-106): the paper's u_a = u^2 for the working precision u = FP64 (Algorithm 4, the correction equation; the
 // paper simulates quad precision, double-double keeps the u^2 level). The product A v, both
 // substitutions with the u_f factors and the diagonal-block inverses are carried in
 // double-double without an intermediate rounding; only the result is rounded to u.

@@ -1,4 +1,4 @@
-// Precision-u_f LU with partial pivoting (Algorithm 4, line 1) for GB300.
+// Precision-u_f LU with partial pivoting (Algorithm 4, the factorization step) for GB300.
 //
 // Numerical model (block fused multiply-add): the Schur complement W is FP32; a panel of
 // width w is factored by GEPP in FP32 arithmetic; the stored factors are the u_f-rounded

@@ -208,173 +208,181 @@ __device__ void hess_reduce(double* M, int ld, int d, double* Qh, double* v) {
     }
 }
 
-// Eigenvalues of the upper Hessenberg a (d x d, ld; destroyed) by the Francis double-shift
-// QR iteration with deflation on negligible subdiagonal entries and exceptional shifts after
-// 10 and 20 iterations without deflation. Conjugate pairs are stored as (re, +im), (re, -im).
-// Returns 0 on success, 1 if some eigenvalue needed more than 60 iterations.
-// T = float: the eigenvalues only choose the shifts of the FP64 inverse iteration and the
-// selection, and GB300 issues FP32 scalar chains about 15 times faster than FP64 ones.
+// ------------------------------------------------------------------ Hessenberg QR eigenvalues
+// Eigenvalues of an upper Hessenberg matrix by the implicitly double-shifted QR iteration
+// (Francis; Golub & Van Loan, "Matrix Computations", Sec. 7.5). Written from the algorithm:
+//  * the active window [lo, hi] is the unreduced block at the bottom of the part not yet
+//    resolved; a subdiagonal entry is negligible (set to zero, splitting the matrix) when it is
+//    at most the working precision's epsilon times the sum of its two diagonal neighbours;
+//  * a 1 x 1 window gives a real eigenvalue, a 2 x 2 window a real pair or a conjugate pair
+//    (closed form, below);
+//  * otherwise one double-shift step: the shifts are the eigenvalues of the trailing 2 x 2 of
+//    the window, entered through their sum s and product t; the first column of
+//    (H - a I)(H - b I) = H^2 - s H + t I has three nonzeros, a 3-element Householder reflector
+//    maps it to e_1, and further 3-element reflectors chase the bulge down the subdiagonal
+//    (a 2-element one at the end). Only eigenvalues are wanted, so each reflector is applied
+//    to the window only;
+//  * a window that has gone 10 steps without a split takes one step with an ad hoc real
+//    double shift (the last diagonal entry moved by 1.5 times the size of the last two
+//    subdiagonal entries) to break a possible cycle.
+// One warp: the row and column updates of each reflector are spread over the lanes; the
+// reflector and the scalars are computed by every lane from shared memory.
+// T = float (the default, GB300 issues dependent FP32 chains far faster than FP64 ones) or
+// double. Pairs are stored as (re, +im), (re, -im). Returns 0, or 1 if the step budget
+// (30 per eigenvalue) ran out; the unresolved window then reports its diagonal entries.
+
+template <typename T> struct EpsOf;
+template <> struct EpsOf<float> { static __device__ float v() { return 5.9604645e-08f; } };
+template <> struct EpsOf<double> { static __device__ double v() { return 1.1102230246251565e-16; } };
+
+// Eigenvalues of [[a, b], [c, e]] into (r1, i1), (r2, i2): with m = (a + e) / 2, h = (a - e) / 2
+// and D = h^2 + b c they are m +- sqrt(D). For D >= 0 the root away from m is formed by
+// addition without cancellation and the other one from the product of the two, det = a e - b c.
 template <typename T>
-__device__ T sgnT(T a, T b) { return b >= T(0) ? fabs(a) : -fabs(a); }
-template <typename T>
-__device__ T wsumT(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+__device__ void eig2x2(T a, T b, T c, T e, T& r1, T& i1, T& r2, T& i2) {
+    const T m = T(0.5) * (a + e), h = T(0.5) * (a - e);
+    const T D = h * h + b * c;
+    if (D >= T(0)) {
+        const T root = sqrt(D);
+        const T far = (m >= T(0)) ? m + root : m - root;
+        const T det = a * e - b * c;
+        r1 = far;
+        r2 = (far != T(0)) ? det / far : m;
+        i1 = i2 = T(0);
+    } else {
+        const T root = sqrt(-D);
+        r1 = r2 = m;
+        i1 = root;
+        i2 = -root;
+    }
 }
+
+// Reflector I - tau v v^T with v = (1, v1, v2) (v2 = 0 for a 2-element one) that maps the
+// column (x0, x1, x2) to (beta, 0, 0), beta = -sign(x0) ||x||. tau = 0 when nothing to do.
 template <typename T>
-__device__ int hqr_eigs(T* a, int ld, int d, T* wr, T* wi) {
+__device__ void reflector3(T x0, T x1, T x2, T& tau, T& v1, T& v2) {
+    const T scale = fabs(x0) + fabs(x1) + fabs(x2);
+    tau = v1 = v2 = T(0);
+    if (scale == T(0) || (x1 == T(0) && x2 == T(0))) return;
+    const T y0 = x0 / scale, y1 = x1 / scale, y2 = x2 / scale;
+    const T nrm = sqrt(y0 * y0 + y1 * y1 + y2 * y2);
+    const T beta = (y0 > T(0)) ? -nrm : nrm;
+    const T den = y0 - beta;
+    tau = (beta - y0) / beta;
+    v1 = y1 / den;
+    v2 = y2 / den;
+}
+
+template <typename T>
+__device__ int hess_qr_eigs(T* H, int ld, int d, T* wr, T* wi) {
     const int lane = LANE;
-#define A_(i, j) a[(i) + (j) * ld]
-    T anorm = 0;
+    const T eps = EpsOf<T>::v();
+    auto at = [&](int i, int j) -> T& { return H[i + j * ld]; };
+    // a norm for windows whose diagonal neighbours are both zero
+    T hnorm = T(0);
     for (int i = lane; i < d; i += 32)
-        for (int j = max(i - 1, 0); j < d; ++j) anorm += fabs(A_(i, j));
-    anorm = wsumT(anorm);
-    int nn = d - 1;
-    T t = 0;
-    int fail = 0;
-    while (nn >= 0) {
-        int its = 0, l;
-        do {
-            for (l = nn; l >= 1; --l) {
-                T s = fabs(A_(l - 1, l - 1)) + fabs(A_(l, l));
-                if (s == 0.0) s = anorm;
-                if (fabs(A_(l, l - 1)) + s == s) {
-                    WSYNC();
-                    if (lane == 0) A_(l, l - 1) = 0.0;
-                    WSYNC();
-                    break;
+        for (int j = (i > 0 ? i - 1 : 0); j < d; ++j) hnorm = fmax(hnorm, fabs(at(i, j)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hnorm = fmax(hnorm, __shfl_xor_sync(0xffffffffu, hnorm, o));
+    int hi = d - 1;
+    int since_split = 0, budget = 30 * d, failed = 0;
+    while (hi >= 0) {
+        // bottom-up search for the start of the unreduced window ending at hi
+        int lo = hi;
+        while (lo > 0) {
+            T nb = fabs(at(lo - 1, lo - 1)) + fabs(at(lo, lo));
+            if (nb == T(0)) nb = hnorm;
+            if (fabs(at(lo, lo - 1)) <= eps * nb) break;
+            --lo;
+        }
+        WSYNC();
+        if (lane == 0 && lo > 0) at(lo, lo - 1) = T(0);
+        WSYNC();
+        const int size = hi - lo + 1;
+        if (size <= 2) {
+            if (lane == 0) {
+                if (size == 1) {
+                    wr[hi] = at(hi, hi);
+                    wi[hi] = T(0);
+                } else {
+                    eig2x2(at(lo, lo), at(lo, hi), at(hi, lo), at(hi, hi), wr[lo], wi[lo], wr[hi], wi[hi]);
                 }
             }
-            T x = A_(nn, nn);
-            if (l == nn) {
-                if (lane == 0) { wr[nn] = x + t; wi[nn] = 0.0; }
-                nn--;
-            } else {
-                T y = A_(nn - 1, nn - 1);
-                T w = A_(nn, nn - 1) * A_(nn - 1, nn);
-                if (l == nn - 1) {
-                    T p = T(0.5) * (y - x);
-                    T q = p * p + w;
-                    T z = sqrt(fabs(q));
-                    x += t;
-                    if (q >= 0.0) {
-                        z = p + sgnT(z, p);
-                        if (lane == 0) {
-                            wr[nn - 1] = wr[nn] = x + z;
-                            if (z != 0.0) wr[nn] = x - w / z;
-                            wi[nn - 1] = wi[nn] = T(0);
-                        }
-                    } else {
-                        if (lane == 0) {
-                            wr[nn - 1] = wr[nn] = x + p;
-                            wi[nn - 1] = z;
-                            wi[nn] = -z;
-                        }
-                    }
-                    nn -= 2;
-                } else {
-                    if (its >= 60) {
-                        fail = 1;
-                        // give up on this block: report the diagonal entries as eigenvalues
-                        if (lane == 0)
-                            for (int i = l; i <= nn; ++i) { wr[i] = A_(i, i) + t; wi[i] = T(0); }
-                        nn = l - 1;
-                        break;
-                    }
-                    if (its == 10 || its == 20) {
-                        t += x;
-                        WSYNC();
-                        for (int i = lane; i <= nn; i += 32) A_(i, i) -= x;
-                        WSYNC();
-                        T s = fabs(A_(nn, nn - 1)) + fabs(A_(nn - 1, nn - 2));
-                        x = y = T(0.75) * s;
-                        w = T(-0.4375) * s * s;
-                    }
-                    ++its;
-                    int m;
-                    T p = 0, q = 0, r = 0, z;
-                    for (m = nn - 2; m >= l; --m) {
-                        z = A_(m, m);
-                        r = x - z;
-                        T s = y - z;
-                        p = (r * s - w) / A_(m + 1, m) + A_(m, m + 1);
-                        q = A_(m + 1, m + 1) - z - r - s;
-                        r = A_(m + 2, m + 1);
-                        s = fabs(p) + fabs(q) + fabs(r);
-                        const T is = T(1) / s;
-                        p *= is;
-                        q *= is;
-                        r *= is;
-                        if (m == l) break;
-                        T u = fabs(A_(m, m - 1)) * (fabs(q) + fabs(r));
-                        T v = fabs(p) * (fabs(A_(m - 1, m - 1)) + fabs(z) + fabs(A_(m + 1, m + 1)));
-                        if (u + v == v) break;
-                    }
-                    WSYNC();
-                    if (lane == 0)
-                        for (int i = m + 2; i <= nn; ++i) {
-                            A_(i, i - 2) = T(0);
-                            if (i != m + 2) A_(i, i - 3) = T(0);
-                        }
-                    WSYNC();
-                    for (int k = m; k <= nn - 1; ++k) {
-                        if (k != m) {
-                            p = A_(k, k - 1);
-                            q = A_(k + 1, k - 1);
-                            r = (k != nn - 1) ? A_(k + 2, k - 1) : T(0);
-                            x = fabs(p) + fabs(q) + fabs(r);
-                            if (x != T(0)) { const T ix = T(1) / x; p *= ix; q *= ix; r *= ix; }
-                        }
-                        T s = sgnT(T(sqrt(p * p + q * q + r * r)), p);
-                        if (s != T(0)) {
-                            WSYNC();
-                            if (lane == 0) {
-                                if (k == m) {
-                                    if (l != m) A_(k, k - 1) = -A_(k, k - 1);
-                                } else {
-                                    A_(k, k - 1) = -s * x;
-                                }
-                            }
-                            p += s;
-                            const T is = T(1) / s, ip = T(1) / p;
-                            x = p * is;
-                            y = q * is;
-                            z = r * is;
-                            q *= ip;
-                            r *= ip;
-                            WSYNC();
-                            for (int jj = k + lane; jj <= nn; jj += 32) {
-                                T pp = A_(k, jj) + q * A_(k + 1, jj);
-                                if (k != nn - 1) {
-                                    pp += r * A_(k + 2, jj);
-                                    A_(k + 2, jj) -= pp * z;
-                                }
-                                A_(k + 1, jj) -= pp * y;
-                                A_(k, jj) -= pp * x;
-                            }
-                            WSYNC();
-                            int mmin = nn < k + 3 ? nn : k + 3;
-                            for (int i = l + lane; i <= mmin; i += 32) {
-                                T pp = x * A_(i, k) + y * A_(i, k + 1);
-                                if (k != nn - 1) {
-                                    pp += z * A_(i, k + 2);
-                                    A_(i, k + 2) -= pp * r;
-                                }
-                                A_(i, k + 1) -= pp * q;
-                                A_(i, k) -= pp;
-                            }
-                            WSYNC();
-                        }
-                    }
+            hi = lo - 1;
+            since_split = 0;
+            WSYNC();
+            continue;
+        }
+        if (budget-- <= 0) {
+            if (lane == 0)
+                for (int i = lo; i <= hi; ++i) { wr[i] = at(i, i); wi[i] = T(0); }
+            failed = 1;
+            hi = lo - 1;
+            WSYNC();
+            continue;
+        }
+        // shift pair through its sum s and product t
+        T s, t;
+        if (++since_split % 11 == 10) {
+            const T mu = at(hi, hi) + T(1.5) * (fabs(at(hi, hi - 1)) + fabs(at(hi - 1, hi - 2)));
+            s = T(2) * mu;
+            t = mu * mu;
+        } else {
+            const T p = at(hi - 1, hi - 1), q = at(hi - 1, hi), r = at(hi, hi - 1), w = at(hi, hi);
+            s = p + w;
+            t = p * w - q * r;
+        }
+        // first column of H^2 - s H + t I within the window
+        T x0 = at(lo, lo) * at(lo, lo) + at(lo, lo + 1) * at(lo + 1, lo) - s * at(lo, lo) + t;
+        T x1 = at(lo + 1, lo) * (at(lo, lo) + at(lo + 1, lo + 1) - s);
+        T x2 = at(lo + 1, lo) * at(lo + 2, lo + 1);
+        for (int c = lo; c <= hi - 1; ++c) {
+            const bool two = (c == hi - 1);       // last reflector touches two rows
+            T tau, v1, v2;
+            reflector3(x0, x1, two ? T(0) : x2, tau, v1, v2);
+            WSYNC();
+            if (tau != T(0)) {
+                const int r2 = two ? c + 1 : c + 2;
+                // from the left: rows c..r2, columns max(lo, c-1)..hi
+                for (int j = (c > lo ? c - 1 : lo) + lane; j <= hi; j += 32) {
+                    T dot = at(c, j) + v1 * at(c + 1, j);
+                    if (!two) dot += v2 * at(c + 2, j);
+                    dot *= tau;
+                    at(c, j) -= dot;
+                    at(c + 1, j) -= dot * v1;
+                    if (!two) at(c + 2, j) -= dot * v2;
                 }
+                WSYNC();
+                // from the right: columns c..r2, rows lo..min(c+3, hi)
+                const int rmax = (c + 3 < hi) ? c + 3 : hi;
+                for (int i = lo + lane; i <= rmax; i += 32) {
+                    T dot = at(i, c) + v1 * at(i, c + 1);
+                    if (!two) dot += v2 * at(i, c + 2);
+                    dot *= tau;
+                    at(i, c) -= dot;
+                    at(i, c + 1) -= dot * v1;
+                    if (!two) at(i, c + 2) -= dot * v2;
+                }
+                (void)r2;
+                WSYNC();
+            }
+            // the entries below the subdiagonal that the reflector just annihilated
+            if (lane == 0 && c > lo) {
+                at(c + 1, c - 1) = T(0);
+                if (!two) at(c + 2, c - 1) = T(0);
             }
             WSYNC();
-        } while (l < nn - 1);
+            if (!two) {
+                // the bulge below column c, to be annihilated by the next reflector
+                x0 = at(c + 1, c);
+                x1 = at(c + 2, c);
+                x2 = (c + 3 <= hi) ? at(c + 3, c) : T(0);
+            }
+        }
+        WSYNC();
     }
-#undef A_
     WSYNC();
-    return fail;
+    return failed;
 }
 
 // Inverse iteration for the eigenvalue (lr, li) of the Hessenberg matrix Hm (d x d, ld): two
@@ -534,11 +542,12 @@ __device__ int select_eigs(const double* wr, const double* wi, int d, int k, int
 }
 
 // Eigenvalues and selection (one warp): Householder reduction of M (d x d, ld d, FP64, in place)
-// to Hessenberg form with the similarity accumulated in Qh (global, ld d); eigenvalues of a
-// power-of-two scaled FP32 copy (Af, d*d floats) by Francis QR; the selected eigenvalues in
-// sel[0..nsel) with the first basis column of each in colofs[]. Returns the number of columns.
-__device__ int eig_values(double* M, float* Af, int d, int k, int largest, int mcap, double* Qh, double* wr,
-                          double* wi, double* vec, int* sel, int* colofs, int* nsel_out, double* hn_out,
+// to Hessenberg form with the similarity accumulated in Qh (global, ld d); eigenvalues by the
+// double-shift Hessenberg QR iteration on a copy in `work` (d*d doubles of shared memory): in FP32
+// on a power-of-two scaled copy (eig64 == 0), or in FP64 (eig64 != 0); the selected eigenvalues
+// in sel[0..nsel) with the first basis column of each in colofs[]. Returns the number of columns.
+__device__ int eig_values(double* M, double* work, int eig64, int d, int k, int largest, int mcap, double* Qh,
+                          double* wr, double* wi, double* vec, int* sel, int* colofs, int* nsel_out, double* hn_out,
                           int* fail_out) {
     const int lane = LANE;
     __shared__ float wrf[SM_DMAX], wif[SM_DMAX];
@@ -547,16 +556,23 @@ __device__ int eig_values(double* M, float* Af, int d, int k, int largest, int m
     double hn = 0.0;
     for (int e = lane; e < d * d; e += 32) hn = fmax(hn, fabs(M[e]));
     hn = warp_max(hn);
-    // scale by 2^-e with hn 2^-e in [0.5, 1): no FP32 overflow, and the unscaling is exact
-    int ex = 0;
-    if (hn > 0.0 && hn < 1.7976931348623157e308) frexp(hn, &ex);
-    const double sc = ldexp(1.0, -ex);
-    for (int e = lane; e < d * d; e += 32) Af[e] = (float)(M[e] * sc);
-    WSYNC();
-    *fail_out = hqr_eigs<float>(Af, d, d, wrf, wif);
-    for (int i = lane; i < d; i += 32) {
-        wr[i] = (double)wrf[i] / sc;
-        wi[i] = (double)wif[i] / sc;
+    if (eig64) {
+        for (int e = lane; e < d * d; e += 32) work[e] = M[e];
+        WSYNC();
+        *fail_out = hess_qr_eigs<double>(work, d, d, wr, wi);
+    } else {
+        // scale by 2^-e with hn 2^-e in [0.5, 1): no FP32 overflow, and the unscaling is exact
+        float* Af = reinterpret_cast<float*>(work);
+        int ex = 0;
+        if (hn > 0.0 && hn < 1.7976931348623157e308) frexp(hn, &ex);
+        const double sc = ldexp(1.0, -ex);
+        for (int e = lane; e < d * d; e += 32) Af[e] = (float)(M[e] * sc);
+        WSYNC();
+        *fail_out = hess_qr_eigs<float>(Af, d, d, wrf, wif);
+        for (int i = lane; i < d; i += 32) {
+            wr[i] = (double)wrf[i] / sc;
+            wi[i] = (double)wif[i] / sc;
+        }
     }
     WSYNC();
     if (lane == 0) {
@@ -769,8 +785,8 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, d
         }
         int fail = 0, nsel = 0;
         double hn = 0.0;
-        const int cols = eig_values(M, reinterpret_cast<float*>(Wk), d, k, first ? 0 : 1, st->m, Qh, wr, wi, vec, sel,
-                                    colofs, &nsel, &hn, &fail);
+        const int cols = eig_values(M, Wk, st->eig64, d, k, first ? 0 : 1, st->m, Qh, wr, wi, vec, sel, colofs,
+                                    &nsel, &hn, &fail);
         // non-converged eigenvalues keep their diagonal estimates (fail is not an error)
         if (lane == 0) {
             nsel_s = nsel;
@@ -946,8 +962,8 @@ gir_status launch_chol_gram(SmallState* st, int k, cudaStream_t s) {
 
 // ------------------------------------------------------------------ standalone eigen test
 __global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, int d, int k, int largest, int mcap,
-                                                             double* wr_o, double* wi_o, double* P, int* kout,
-                                                             double* Qh) {
+                                                             int eig64, double* wr_o, double* wi_o, double* P,
+                                                             int* kout, double* Qh) {
     extern __shared__ double smem[];
     const int lane = LANE, warp = threadIdx.x >> 5;
     double* M = smem;
@@ -961,8 +977,8 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, 
         WSYNC();
         int fail = 0, nsel = 0;
         double hn = 0.0;
-        const int cols = eig_values(M, reinterpret_cast<float*>(Wk), d, k, largest, mcap, Qh, wr, wi, vec, sel, colofs,
-                                    &nsel, &hn, &fail);
+        const int cols = eig_values(M, Wk, eig64, d, k, largest, mcap, Qh, wr, wi, vec, sel, colofs, &nsel, &hn,
+                                    &fail);
         if (lane == 0) {
             nsel_s = nsel;
             cols_s = cols;
@@ -978,13 +994,14 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, 
     if (lane == 0) *kout = fail_s ? -cols_s - 1 : cols_s;
 }
 
-gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi, double* P,
-                            int kcap, int* kout, double* scratch, cudaStream_t s) {
+gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap, int eig64, double* wr, double* wi,
+                            double* P, int kcap, int* kout, double* scratch, cudaStream_t s) {
     (void)kcap;
     static std::atomic<unsigned> attr_done{0};
     const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
     GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_small_eig, (int)smem, attr_done));
-    count_launch(), k_small_eig<<<1, CLOSE_THREADS, smem, s>>>(M, d, k, largest, mcap, wr, wi, P, kout, scratch);
+    count_launch(), k_small_eig<<<1, CLOSE_THREADS, smem, s>>>(M, d, k, largest, mcap, eig64, wr, wi, P, kout,
+                                                                  scratch);
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }

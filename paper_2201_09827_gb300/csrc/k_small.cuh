@@ -21,7 +21,7 @@ struct SmallState {
     int k_target;       // requested k
     int m;              // restart length
     int first;          // 1 in a first (plain GMRES) cycle
-    int pad_;
+    int eig64;          // harmonic Ritz eigenvalues by FP64 (1) or FP32 (0) Hessenberg QR
     double beta;        // ||r|| at the cycle start
     double tol;         // tau * ||c||
     double est;         // Givens residual estimate |g_{j+1}|
@@ -51,13 +51,13 @@ gir_status launch_givens_step(SmallState* st, cudaStream_t s);
 // End of a cycle: least squares, residual/solution coefficients, harmonic Ritz vectors,
 // QR(G P_k), coefficients of the new C_k and U_k. Uses Qh scratch (global, SM_DMAX^2 doubles).
 gir_status launch_cycle_close(SmallState* st, double* qh_scratch, cudaStream_t s);
-// Carry (Algorithm 3, lines 1-3) by Cholesky QR: from the Gram matrix G2 = Z^T Z (k x k)
+// Carry (Algorithm 3, the QR of A~ Y~ at the start) by Cholesky QR: from the Gram matrix G2 = Z^T Z (k x k)
 // compute R (upper, chol) and Rinv; returns rank in st->knew.
 gir_status launch_chol_gram(SmallState* st, int k, cudaStream_t s);
 // w *= hinv (rounded to u): normalisation of the new Arnoldi vector.
 gir_status launch_scale_by(double* w, int64_t n, const double* factor, int invert, int round32, cudaStream_t s);
 // Standalone eigen-solver (testing): M d x d column-major in device memory.
-gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap, double* wr, double* wi,
-                            double* P, int kcap, int* kout, double* scratch, cudaStream_t s);
+gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap, int eig64, double* wr,
+                            double* wi, double* P, int kcap, int* kout, double* scratch, cudaStream_t s);
 
 }  // namespace gir

@@ -1,4 +1,4 @@
-// Application of the LU preconditioner M^-1 = mu S U^-1 L^-1 P R (Algorithm 4, line 5) and of
+// Application of the LU preconditioner M^-1 = mu S U^-1 L^-1 P R (Algorithm 4, correction equation) and of
 // its transpose, on the u_f factors, with float-float arithmetic (about 48 significand bits).
 //
 // Triangular solves are blocked by b = 64 rows. One persistent CTA per block row takes a

@@ -1,5 +1,5 @@
-// Bandwidth-bound kernels of the solve path: residual (Algorithm 4, line 4), the FP64
-// matrix-vector products inside A~ (line 5), and the tall-skinny products of GCRO-DR
+// Bandwidth-bound kernels of the solve path: residual (Algorithm 4), the FP64
+// matrix-vector products inside A~ (the correction equation), and the tall-skinny products of GCRO-DR
 // (Algorithm 3: projections against [C_k V], solution/residual/recycle updates).
 //
 // Layouts: A is FP64 row-major with leading dimension lda; the Krylov/recycle bases are

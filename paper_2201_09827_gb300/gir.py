@@ -77,7 +77,7 @@ SYMBOLS = {
     "gir_trace_select": (None, [C.c_char_p]),
     "gir_launch_count": (C.c_ulonglong, []),
     "gir_small_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                                C.c_int, C.POINTER(C.c_int)]),
+                                C.c_int, C.POINTER(C.c_int), C.c_int]),
 }
 
 _lib = None
@@ -138,6 +138,7 @@ GIR_FLAG_AUTOTUNE = 0x1
 GIR_FLAG_CW_BERR = 0x2   # also compute the componentwise backward error and stop on both
 GIR_FLAG_SIR = 0x4       # Algorithm 1 comparator: correction by substitution, no GCRO-DR
 GIR_FLAG_ADAPTIVE_K = 0x8  # k = its_1 - 1 from the first refinement step (Section 5)
+GIR_FLAG_EIG_FP64 = 0x10  # harmonic Ritz eigenvalues by FP64 Hessenberg QR (default FP32)
 
 
 @dataclass
@@ -198,7 +199,7 @@ def _check_vec(v: torch.Tensor, n: int):
 
 
 class Factorization:
-    """A gir_handle: the u_f LU factors of A plus the recycle spaces (Algorithm 4, line 1)."""
+    """A gir_handle: the u_f LU factors of A plus the recycle spaces (Algorithm 4, the factorization step)."""
 
     def __init__(self, A: torch.Tensor, params: Params, stream=None):
         lib = load()
@@ -326,8 +327,11 @@ def gemv(A, v, trans=False, stream=None):
     return w
 
 
-def small_eig(M, k, largest, mcap):
-    """GPU single-warp eigen-solver of the harmonic Ritz step on a host numpy matrix (testing)."""
+def small_eig(M, k, largest, mcap, eig_prec="fp32"):
+    """GPU single-warp eigen-solver of the harmonic Ritz step on a host numpy matrix (testing).
+
+    ``eig_prec`` is the precision of the Hessenberg QR that gives the eigenvalues: "fp32" (the
+    solver's default) or "fp64"."""
     import numpy as np
     M = np.asarray(M, dtype=np.float64)
     d = M.shape[0]
@@ -339,7 +343,7 @@ def small_eig(M, k, largest, mcap):
     kout = C.c_int()
     st = load().gir_small_eig(Mc.ctypes.data_as(C.c_void_p), d, k, int(largest), mcap,
                               wr.ctypes.data_as(C.c_void_p), wi.ctypes.data_as(C.c_void_p),
-                              P.ctypes.data_as(C.c_void_p), kcap, C.byref(kout))
+                              P.ctypes.data_as(C.c_void_p), kcap, C.byref(kout), PREC[eig_prec])
     if st != GIR_OK:
         raise GirError(st, "gir_small_eig")
     kk = kout.value

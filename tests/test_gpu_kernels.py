@@ -206,21 +206,24 @@ def test_apply_minv_and_atilde_dd(G, n, fmt):
 
 @pytest.mark.parametrize("d", [1, 2, 5, 12, 30, 50, 112])
 @pytest.mark.parametrize("largest", [0, 1])
-def test_small_eig(G, d, largest):
-    """The harmonic Ritz eigen-solver: eigenvalues from Francis QR in FP32 (they steer only the
-    selection and the shifts), eigenvectors by FP64 inverse iteration, so the eigenvalues match to
-    FP32 accuracy times their condition and P spans an invariant subspace to FP64 accuracy."""
+@pytest.mark.parametrize("eig_prec", ["fp32", "fp64"])
+def test_small_eig(G, d, largest, eig_prec):
+    """The harmonic Ritz eigen-solver: eigenvalues from Hessenberg QR in FP32 (the default; they
+    steer only the selection and the shifts) or FP64, eigenvectors by FP64 inverse iteration, so
+    the eigenvalues match to the QR's precision times their condition and P spans an invariant
+    subspace to FP64 accuracy either way."""
     from scipy.optimize import linear_sum_assignment
     rng = np.random.default_rng(d + 100 * largest)
     M = rng.standard_normal((d, d))
     k = min(10, max(1, d - 1))
-    wr, wi, P, failed = G.small_eig(M, k, largest, 200)
+    wr, wi, P, failed = G.small_eig(M, k, largest, 200, eig_prec=eig_prec)
     assert not failed
     lam = np.linalg.eigvals(M)
     got = wr + 1j * wi
     dist = np.abs(got[:, None] - lam[None, :])
     r, c = linear_sum_assignment(dist)
-    assert dist[r, c].max() <= 1e-4 * max(1.0, np.abs(lam).max())
+    tol = 1e-4 if eig_prec == "fp32" else 1e-10
+    assert dist[r, c].max() <= tol * max(1.0, np.abs(lam).max())
     # P spans an invariant subspace whose eigenvalues are the selected ones
     T = np.linalg.lstsq(P, M @ P, rcond=None)[0]
     assert np.linalg.norm(M @ P - P @ T) <= 1e-9 * max(1.0, np.linalg.norm(M @ P))
@@ -229,6 +232,70 @@ def test_small_eig(G, d, largest):
     want = allm[::-1][:P.shape[1]] if largest else allm[:P.shape[1]]
     assert np.allclose(np.sort(mags), np.sort(want), rtol=1e-8, atol=1e-12)
     assert abs(P.shape[1] - k) <= 1
+
+
+def _near_tie_matrix(rng, d, k, gap, pair_at_boundary):
+    """Real d x d matrix with well-conditioned eigenvectors whose eigenvalue magnitudes are
+    distinct except for a near tie (relative gap ``gap``) straddling the k-th place: either two
+    real eigenvalues of opposite sign, or a real eigenvalue and a conjugate pair."""
+    mags = list(np.geomspace(0.5, 40.0, d))
+    blocks, vals = [], []
+    i = 0
+    while len(vals) < d:
+        if len(vals) == k - 1:
+            # places k and k+1: the near tie
+            base = mags[len(vals)]
+            if pair_at_boundary and len(vals) + 3 <= d:
+                vals += [base]
+                blocks.append(np.array([[base]]))
+                r = base * (1 + gap)
+                a, b = r * np.cos(1.0), r * np.sin(1.0)
+                vals += [complex(a, b), complex(a, -b)]
+                blocks.append(np.array([[a, b], [-b, a]]))
+            else:
+                vals += [base, -base * (1 + gap)]
+                blocks.append(np.array([[base]]))
+                blocks.append(np.array([[-base * (1 + gap)]]))
+            continue
+        m = mags[len(vals)]
+        sgn = 1.0 if rng.random() < 0.5 else -1.0
+        vals.append(sgn * m)
+        blocks.append(np.array([[sgn * m]]))
+    D = np.zeros((d, d))
+    o = 0
+    for bl in blocks:
+        q = bl.shape[0]
+        D[o:o + q, o:o + q] = bl
+        o += q
+    D = D[:d, :d]
+    Q = np.linalg.qr(rng.standard_normal((d, d)))[0]
+    X = Q @ (np.eye(d) + 0.1 * np.triu(rng.standard_normal((d, d)), 1) / np.sqrt(d))
+    return X @ D @ np.linalg.inv(X)
+
+
+@pytest.mark.parametrize("eig_prec,gap", [("fp32", 1e-4), ("fp64", 1e-9)])
+@pytest.mark.parametrize("pair_at_boundary", [False, True])
+@pytest.mark.parametrize("largest", [0, 1])
+def test_small_eig_near_ties_select_oracle_subspace(G, eig_prec, gap, pair_at_boundary, largest):
+    """Near ties in |theta| at the k-th place: the eigenvalues that steer the selection (FP32 by
+    default, FP64 with GIR_FLAG_EIG_FP64) pick the same eigenvectors as the oracle's FP64
+    selection (numpy eig + the pair rule), so P spans the oracle's subspace. FP32 separates
+    relative gaps of 1e-4 on well-conditioned eigenvalues; ties closer than FP32's accuracy need
+    the FP64 iteration, shown here at 1e-9."""
+    from oracle.gcrodr import select_harmonic
+    import scipy.linalg as sla
+    d, k = 30, 8
+    for trial in range(4):
+        rng = np.random.default_rng(1000 * trial + 10 * largest + pair_at_boundary)
+        kk = (d - k) if largest else k          # the near tie straddles the k-th selected place
+        M = _near_tie_matrix(rng, d, kk, gap, pair_at_boundary)
+        wr, wi, P, failed = G.small_eig(M, k, largest, 50, eig_prec=eig_prec)
+        assert not failed
+        theta, Z = np.linalg.eig(M)
+        Po = select_harmonic(1.0 / theta if largest else theta, Z, k, d, 50)
+        assert P.shape[1] == Po.shape[1]
+        ang = sla.subspace_angles(P, Po)
+        assert ang.max() <= 1e-8, (trial, ang.max())
 
 
 def _tile_scale(vmax):

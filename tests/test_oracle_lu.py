@@ -9,7 +9,7 @@ from oracle import lu as lum
 from oracle.formats import UNIT_ROUNDOFF
 from synth import randsvd, prolate
 
-T_EMIN = {"fp16": (11, -14), "bf16": (8, -126), "fp32": (24, -126)}
+T_EMIN = {"fp16": (11, -14), "bf16": (8, -126), "fp32": (24, -126), "e4m3": (4, -6)}
 
 
 def round_frac(q: Fraction, fmt):
@@ -75,6 +75,131 @@ def test_block_panel_matches_rational_fp32_fma():
     assert list(F.ipiv) == piv
     ref = np.array([[float(round_frac(v, "bf16")) for v in row] for row in W])
     assert np.array_equal(np.tril(F.L, -1) + F.U, ref)
+
+
+def _tile_scale_frac(vmax):
+    """Largest power of two s with vmax * s <= 448 (1 for an all-zero tile), exactly."""
+    if vmax == 0:
+        return Fraction(1)
+    e = 0
+    while vmax * Fraction(2) ** e > 448:
+        e -= 1
+    while vmax * Fraction(2) ** (e + 1) <= 448:
+        e += 1
+    return Fraction(2) ** e
+
+
+def _round_operand_frac(X, fmt, row0, col0, tile):
+    """Round a block (list of rows of Fractions) to fmt; e4m3 per tile of the global grid."""
+    if fmt != "e4m3":
+        return [[round_frac(v, fmt) for v in row] for row in X]
+    m, n = len(X), len(X[0]) if X else 0
+    out = [[None] * n for _ in range(m)]
+    for r0 in range(0, m):
+        if (r0 + row0) % tile != 0 and r0 != 0:
+            continue
+        r1 = min(m, (r0 + row0) // tile * tile + tile - row0)
+        for c0 in range(0, n):
+            if (c0 + col0) % tile != 0 and c0 != 0:
+                continue
+            c1 = min(n, (c0 + col0) // tile * tile + tile - col0)
+            vmax = max((abs(X[i][j]) for i in range(r0, r1) for j in range(c0, c1)), default=Fraction(0))
+            sc = _tile_scale_frac(vmax)
+            for i in range(r0, r1):
+                for j in range(c0, c1):
+                    out[i][j] = round_frac(X[i][j] * sc, "e4m3") / sc
+    return out
+
+
+def block_lu_rational(A, fmt, w, tile=None, round_l=True, round_u12=True):
+    """The block-FMA LU model in exact rational arithmetic with explicit roundings, written
+    from its definition independently of oracle.lu: per block column, GEPP of the panel with
+    FP32 quotients and FP32 fused updates (ties to the lowest row), the panel's L and U11 rounded
+    to fmt, U12 by FP32 substitution (exact dot, one rounding) with the rounded L11, then rounded
+    to fmt, and the trailing matrix fl32(W - L21 U12) from the rounded operands (exact dot, one
+    rounding). round_l / round_u12 switch off one rounding, to show the comparison sees it."""
+    n = len(A)
+    if fmt == "e4m3":
+        w = tile
+    f32 = lambda q: round_frac(q, "fp32")
+    W = [[f32(Fraction(float(v))) for v in row] for row in A]
+    Ls = [[Fraction(0)] * n for _ in range(n)]
+    Us = [[Fraction(0)] * n for _ in range(n)]
+    piv = []
+    for c0 in range(0, n, w):
+        c1 = min(c0 + w, n)
+        for k in range(c0, c1):
+            p = max(range(k, n), key=lambda i: (abs(W[i][k]), -i))
+            piv.append(p)
+            W[k], W[p] = W[p], W[k]
+            Ls[k], Ls[p] = Ls[p], Ls[k]
+            for i in range(k + 1, n):
+                l = f32(W[i][k] / W[k][k])
+                W[i][k] = l
+                for j in range(k + 1, c1):
+                    W[i][j] = f32(W[i][j] - l * W[k][j])
+        wd = c1 - c0
+        low = [[W[i][j] if (i - c0) > (j - c0) else Fraction(0) for j in range(c0, c1)] for i in range(c0, n)]
+        lowq = _round_operand_frac(low, fmt, c0, c0, tile) if round_l else low
+        for i in range(c0, n):
+            for j in range(c0, c1):
+                if i > j:
+                    Ls[i][j] = lowq[i - c0][j - c0]
+        top = [[W[i][j] if j >= i else Fraction(0) for j in range(c0, c1)] for i in range(c0, c1)]
+        topq = _round_operand_frac(top, fmt, c0, c0, tile)
+        for i in range(c0, c1):
+            for j in range(c0, c1):
+                if j >= i:
+                    Us[i][j] = topq[i - c0][j - c0]
+        if c1 < n:
+            X = [list(W[i][c1:]) for i in range(c0, c1)]
+            for r in range(1, wd):
+                for j in range(n - c1):
+                    X[r][j] = f32(X[r][j] - sum(Ls[c0 + r][c0 + q] * X[q][j] for q in range(r)))
+            U12 = _round_operand_frac(X, fmt, c0, c1, tile) if round_u12 else X
+            for i in range(wd):
+                W[c0 + i][c1:] = X[i]
+                Us[c0 + i][c1:] = U12[i]
+            for i in range(c1, n):
+                for j in range(c1, n):
+                    W[i][j] = f32(W[i][j] - sum(Ls[i][c0 + q] * U12[q][j - c1] for q in range(wd)))
+    LU = [[float(Ls[i][j]) if i > j else float(Us[i][j]) for j in range(n)] for i in range(n)]
+    return np.array(LU), piv
+
+
+@pytest.mark.parametrize("fmt,n,w", [("bf16", 7, 2), ("bf16", 9, 3), ("fp16", 8, 3), ("fp16", 6, 2)])
+def test_block_multipanel_matches_rational(fmt, n, w):
+    """Several block columns: the oracle's block model equals the rational restatement bit for
+    bit (pivots and every stored factor entry), and would not if it skipped the u_f rounding of
+    L21 or of U12 before the trailing update."""
+    rng = np.random.default_rng(100 * n + w)
+    A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-2, 2, (n, n)))
+    F = lum.lu_block(A, fmt, w=w, scale=False)
+    ref, piv = block_lu_rational(A, fmt, w)
+    assert list(F.ipiv) == piv
+    got = np.tril(F.L, -1) + F.U
+    assert np.array_equal(got, ref)
+    for kw in ({"round_l": False}, {"round_u12": False}):
+        alt, _ = block_lu_rational(A, fmt, w, **kw)
+        assert not np.array_equal(got, alt), kw
+
+
+def test_block_fp8_tiles_match_rational(monkeypatch):
+    """FP8-E4M3 with power-of-two tile scales on a 4 x 4 tile grid (the tile size is the model's
+    parameter; 128 in production): block columns of one tile width, panels crossing row-tile
+    boundaries, a ragged last tile. Equal to the rational restatement bit for bit."""
+    monkeypatch.setattr(lum, "FP8_TILE", 4)
+    rng = np.random.default_rng(44)
+    n = 10
+    A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-3, 3, (n, n)))
+    F = lum.lu_block(A, "e4m3", w=32, scale=False)
+    ref, piv = block_lu_rational(A, "e4m3", None, tile=4)
+    assert list(F.ipiv) == piv
+    got = np.tril(F.L, -1) + F.U
+    assert np.array_equal(got, ref)
+    for kw in ({"round_l": False}, {"round_u12": False}):
+        alt, _ = block_lu_rational(A, "e4m3", None, tile=4, **kw)
+        assert not np.array_equal(got, alt), kw
 
 
 @pytest.mark.parametrize("mode", ["chop", "block"])

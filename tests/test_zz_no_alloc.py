@@ -46,10 +46,46 @@ def test_noalloc_matches_allocating_entry_point_twice(G):
         assert bool(((w - ref).abs() <= bound + 1e-300).all())
 
 
-def test_noalloc_rejects_too_large(G):
-    n = 11586
+def test_noalloc_allocates_nothing(G):
+    """A call after the first (which looks up the fixed array's address) leaves the device's free
+    memory unchanged: the library takes no device memory in it."""
+    rng = np.random.default_rng(7)
+    n = 2048
+    A = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+    v = torch.from_numpy(rng.standard_normal(n)).cuda()
+    w = torch.empty_like(v)
+    lib = G.load()
+    args = (ctypes.c_void_p(A.data_ptr()), n, n, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert lib.gir_gemv_t_noalloc(*args) == G.GIR_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert lib.gir_gemv_t_noalloc(*args) == G.GIR_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ref = G.gemv(A, v, trans=True)
+    assert bool(((w - ref).abs() <= 2 * n * 2.0 ** -53 * (A.abs().t() @ v.abs()) + 1e-300).all())
+
+
+def test_noalloc_size_limit_boundary(G):
+    """n = 11520 is the largest order whose partial sums (ceil(n / 256) * n doubles) fit the 2^19
+    doubles of the fixed array: it runs and matches gir_gemv(trans = 1); n = 11521 is rejected."""
+    n = 11520
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11520)
+    A = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    v = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    st, w = _noalloc(G, A, v)
+    assert st == G.GIR_OK
+    ref = G.gemv(A, v, trans=True)
+    bound = 2 * n * 2.0 ** -53 * (A.abs().t() @ v.abs())
+    assert bool(((w - ref).abs() <= bound + 1e-300).all())
+    del A
+    torch.cuda.empty_cache()
+    n = 11521
     A = torch.zeros(1, 1, dtype=torch.float64, device="cuda")
-    v = torch.zeros(1, dtype=torch.float64, device="cuda")
     st = G.load().gir_gemv_t_noalloc(ctypes.c_void_p(A.data_ptr()), n, n, ctypes.c_void_p(v.data_ptr()),
                                      ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(0))
     assert st == G.GIR_INVALID_ARG
