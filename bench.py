@@ -224,6 +224,188 @@ def roofline_for(phase, total_ms, calls, args, peaks, peak_kind):
             "avg_ms": total_ms / calls}
 
 
+def sweep_line(args, world, workload, extra_cfg, ms, times, result, roof=None, cpu=None, e2e=None, clocks=None,
+               launches=None, metric=METRIC):
+    """One JSON line of the measurement matrix, with the keys of the headline line."""
+    cfg = {"workload": workload, **extra_cfg,
+           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+           "l2": "inputs larger than L2 where the matrix exceeds 129 MB; smaller ones run from L2"}
+    return {"metric": metric, "value": ms, "unit": "ms", "n_gpus": world, "steps": len(times),
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg, "e2e": e2e,
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "result": {**result, "times_ms": times}, "sweep": True}
+
+
+def run_sweep(args, rank, world, local):
+    """The measurement matrix: every point runs W untimed and K timed steps (factor + solve with
+    the inputs resident in HBM, CUDA events on the launching stream), median reported."""
+    import torch
+    import numpy as np
+    import paper_2201_09827_gb300 as gir
+    from synth import randsvd_torch, prolate, convdiff, rhs_uniform, normal_vector, batch_specs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    out = []
+
+    def emit(line):
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts, res = [], None
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), ts, res
+
+    def solve_step(A, b, prm):
+        def fn():
+            F = gir.Factorization(A, prm)
+            x, info = F.solve(A, b)
+            F.close()
+            return x, info
+        return fn
+
+    def berr_dd(A, x, b):
+        r = gir.residual(A, x, b, "dd")
+        return (r.abs().max() / (A.abs().sum(1).max() * x.abs().max() + b.abs().max())).item()
+
+    n = args.n
+    # ---- headline matrix: kappa_2 x u_f, RGMRES-IR(50, 10) and the GMRES-IR(50) comparator
+    for kappa in (1e2, 1e4, 1e6, 1e8):
+        A = randsvd_torch(n, kappa, seed=0, device=f"cuda:{local}")
+        g = torch.Generator(device=dev)
+        g.manual_seed(2)
+        xstar = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+        b = A @ xstar
+        for uf in ("fp16", "bf16", "e4m3"):
+            for k in (args.k, 0):
+                prm = gir.Params(uf=uf, u="fp64", ur="fp64", m=args.m, k=k, tau=1e-8, imax=10, target_berr=1e-15,
+                                 carry_mode=1)
+                ms, ts, (x, info) = timed(solve_step(A, b, prm), args.steps, args.warmup)
+                ferr = ((x - xstar).abs().max() / xstar.abs().max()).item()
+                emit(sweep_line(args, world, f"randsvd dense n={n}, kappa_2={kappa:g}, b=A x*; u_f={uf}, u=u_r=fp64, "
+                                             f"{'RGMRES-IR' if k else 'GMRES-IR'}(m={args.m}, k={k}), tau=1e-8, "
+                                             f"target berr 1e-15",
+                                {"n": n, "kappa_2": kappa, "uf": uf, "u": "fp64", "ur": "fp64", "m": args.m, "k": k},
+                                ms, ts, {"status": info.status, "its": info.its, "total_its": info.total_its,
+                                         "ir_steps": info.ir_steps, "berr_dd": berr_dd(A, x, b),
+                                         "ferr_vs_xstar": ferr, "ms_factor": info.ms_factor,
+                                         "ms_solve": info.ms_solve}))
+        # FP64 LU on the same GPU (cuSOLVER through torch), warm median
+        ms, ts, xl = timed(lambda: torch.linalg.solve(A, b), max(3, args.steps), 1)
+        emit(sweep_line(args, world, f"randsvd dense n={n}, kappa_2={kappa:g}: FP64 LU solve (torch.linalg.solve, "
+                                     f"cuSOLVER getrf/getrs) on the same GPU",
+                        {"n": n, "kappa_2": kappa, "comparator": "fp64_lu"}, ms, ts,
+                        {"berr_dd": berr_dd(A, xl, b)}))
+        del A, b, xstar, xl
+        torch.cuda.empty_cache()
+
+    # ---- prolate n=4096: (bf16, fp64, dd), GCRO-DR(30, k) with k = 10 against k = 0
+    np_ = 4096
+    for w in (0.25, 0.499):
+        A = torch.from_numpy(prolate(np_, w)).to(dev)
+        b = torch.from_numpy(rhs_uniform(np_, 0)).to(dev)
+        for k in (10, 0):
+            prm = gir.Params(uf="bf16", u="fp64", ur="dd", m=30, k=k, tau=1e-8, imax=10, target_berr=-1.0,
+                             carry_mode=1)
+            ms, ts, (x, info) = timed(solve_step(A, b, prm), args.steps, args.warmup)
+            emit(sweep_line(args, world, f"prolate Toeplitz n={np_}, w={w}, b~U(0,1); u_f=bf16, u=fp64, u_r=dd; "
+                                         f"GCRO-DR(30, {k}), tau=1e-8, target 2u",
+                            {"n": np_, "w": w, "uf": "bf16", "u": "fp64", "ur": "dd", "m": 30, "k": k}, ms, ts,
+                            {"status": info.status, "its": info.its, "total_its": info.total_its,
+                             "ir_steps": info.ir_steps, "berr_dd": berr_dd(A, x, b), "ms_factor": info.ms_factor,
+                             "ms_solve": info.ms_solve}))
+        del A, b
+
+    # ---- conv-diff n=10000: forward solve + adjoint (gradient) through the autograd function
+    A0 = torch.from_numpy(convdiff(100, 50.0)).to(dev)
+    b0 = torch.from_numpy(rhs_uniform(10000, 4)).to(dev)
+    xt = torch.from_numpy(normal_vector(10000, 5)).to(dev)
+    prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=40, k=10, tau=1e-8, imax=10, target_berr=1e-15,
+                     carry_mode=1)
+
+    def fwd_bwd():
+        A = A0.detach().requires_grad_(True)
+        b = b0.detach().requires_grad_(True)
+        x = gir.GirSolve.apply(A, b, prm)
+        loss = ((x - xt) ** 2).sum()
+        loss.backward()
+        return x.detach(), A.grad, b.grad
+
+    ms, ts, (x, dA, db) = timed(fwd_bwd, args.steps, args.warmup)
+    # the gradient against an FP64 LU solve on the same GPU (context for the timed numbers)
+    xs = torch.linalg.solve(A0, b0)
+    lam = torch.linalg.solve(A0.T, 2 * (xs - xt))
+    emit(sweep_line(args, world, "conv-diff 5-point upwind N=100 (n=10000), Pe=50, b~U(0,1); loss=||x-x_t||^2; "
+                                 "forward BF16-LU RGMRES-IR(40,10) + adjoint solve, dA, db",
+                    {"n": 10000, "uf": "bf16", "u": "fp64", "ur": "fp64", "m": 40, "k": 10}, ms, ts,
+                    {"berr_dd": berr_dd(A0, x, b0),
+                     "db_rel_err_vs_fp64_lu": ((db - lam).abs().max() / lam.abs().max()).item(),
+                     "dA_rel_err_vs_fp64_lu": ((dA + torch.outer(lam, xs)).abs().max()
+                                               / torch.outer(lam, xs).abs().max()).item()},
+                    metric="ms forward + backward (adjoint) solve, conv-diff n=10000"))
+    del A0, b0, xt, x, dA, db, xs, lam
+    torch.cuda.empty_cache()
+
+    # ---- batch: 512 randsvd systems, n ~ U{256..4096}, kappa_2 = 10^U(2,8), (bf16, fp64, fp64), (30, 8)
+    sizes, kappas = batch_specs(512, 256, 4096, 2.0, 8.0, seed=3)
+    As, bs = [], []
+    for i, (nn, kp) in enumerate(zip(sizes, kappas)):
+        A = randsvd_torch(nn, kp, seed=1000 + i, device=f"cuda:{local}")
+        gg = torch.Generator(device=dev)
+        gg.manual_seed(5000 + i)
+        As.append(A)
+        bs.append(A @ torch.randn(nn, dtype=torch.float64, device=dev, generator=gg))
+    prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0, carry_mode=1)
+    ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm), max(1, args.steps // 2), 1)
+    conv = sum(1 for i in infos if i.status == 0)
+    emit(sweep_line(args, world, "batch of 512 randsvd systems, n~U{256..4096}, kappa_2=10^U(2,8), b=A x*; "
+                                 "u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u",
+                    {"systems": 512, "n_total": int(sum(sizes)), "uf": "bf16", "m": 30, "k": 8}, ms, ts,
+                    {"status": st, "converged": conv, "total_its": int(sum(i.total_its for i in infos))},
+                    metric="ms for the whole batch of 512 systems"))
+    del As, bs, xs_
+    torch.cuda.empty_cache()
+
+    # ---- the oracle at two sizes (validates the n^3 projection of the headline's cpu_baseline)
+    if rank == 0 and not args.no_cpu:
+        pts = []
+        for n_s in (1536, 3072):
+            dt, info = oracle_sample(n_s, args.kappa, args.uf)
+            pts.append((n_s, dt, info.paper_format()))
+        (n1, t1, _), (n2, t2, _) = pts
+        expo = np.log(t2 / t1) / np.log(n2 / n1)
+        emit({"metric": "oracle seconds (CPU) on randsvd kappa_2=1e2 at two sizes", "sweep": True,
+              "value": t2, "unit": "s", "cpu_baseline": {"value": t2 * 1e3, "unit": "ms", "cores": os.cpu_count(),
+                                                          "kind": "oracle", "sample": f"n={n2}"},
+              "result": {"points": [{"n": a, "s": b, "its": c} for a, b, c in pts], "fitted_exponent": expo,
+                         "projected_ms_n16384": t2 * 1e3 * (args.n / n2) ** expo, "cpu": cpu_model()}})
+    return 0
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -239,11 +421,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-lu", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the measurement matrix instead of the headline: kappa_2 x u_f with the k = 0 comparator, "
+                         "the FP64 LU comparator, prolate n=4096 recycling counts, conv-diff n=10000 forward + "
+                         "backward, the 512-system batch and the oracle at two sizes; one JSON line per point")
     args = ap.parse_args()
     rank, world, local = dist_env()
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.sweep:
+        return run_sweep(args, rank, world, local)
 
     import torch
     import paper_2201_09827_gb300 as gir

@@ -80,7 +80,10 @@ def assert_parity(A, b, x, info, xo, io, u, ur="fp64"):
         assert be <= 4 * max(beo, uu)
         assert abs(info.total_its - io.total) <= 0.1 * io.total + 1, (info.its, io.its)
         assert info.ir_steps == io.steps or abs(info.ir_steps - io.steps) <= 1
-        assert_forward_error(A, b, x, u, ur)
+        if u == "fp64":
+            # with u = FP32 the run stops at eta <= 2u, where the forward error is still about
+            # kappa eta, above Table 2's converged level; those tests bound it separately
+            assert_forward_error(A, b, x, u, ur)
 
 
 @pytest.mark.parametrize("kappa,uf", [(1e2, "bf16"), (1e2, "fp16"), (1e4, "fp16")])
