@@ -115,13 +115,34 @@ def oracle_sample(n_s=3072, kappa=1e2, uf="bf16"):
     return dt, info
 
 
+def oracle_projection(n, n_s, kappa, uf):
+    """The oracle at n_s / 2 and n_s; the time at n from the exponent fitted to the two points
+    (the LU is O(n^3), the refinement O(n^2) per iteration, so the exponent lies between)."""
+    import math
+    t1, i1 = oracle_sample(n_s // 2, kappa, uf)
+    t2, i2 = oracle_sample(n_s, kappa, uf)
+    expo = math.log(t2 / t1) / math.log(2.0)
+    return t2 * (n / n_s) ** expo, t1, t2, expo, i1, i2
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline_json(n, n_s, kappa, uf):
-    dt, info = oracle_sample(n_s, kappa, uf)
-    scale = (n / n_s) ** 3
-    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle RGMRES-IR (numpy FP64, u_f by rounding) on randsvd n={n_s}, kappa_2={kappa:g}, "
-                      f"{uf}, GCRO-DR(50,10): {dt:.2f} s measured ({info.paper_format()}), scaled by "
-                      f"(n/{n_s})^3 = {scale:.0f} to n={n}"}
+    proj, t1, t2, expo, i1, i2 = oracle_projection(n, n_s, kappa, uf)
+    return {"value": proj * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle RGMRES-IR (numpy FP64, u_f by rounding) on randsvd kappa_2={kappa:g}, {uf}, "
+                      f"GCRO-DR(50,10) at n={n_s // 2} ({t1:.2f} s, {i1.paper_format()}) and n={n_s} "
+                      f"({t2:.2f} s, {i2.paper_format()}); time at n={n} projected with the fitted exponent "
+                      f"{expo:.2f}; host CPU {cpu_model()}"}
 
 
 def run_reference(args, rank, world):
@@ -131,12 +152,15 @@ def run_reference(args, rank, world):
     vals = []
     for _ in range(args.warmup):
         oracle_sample(max(256, n_s // 4), args.kappa, args.uf)
+    expos = []
     for _ in range(args.steps):
-        dt, info = oracle_sample(n_s, args.kappa, args.uf)
-        vals.append(dt * 1e3 * (args.n / n_s) ** 3)
+        proj, t1, t2, expo, _, _ = oracle_projection(args.n, n_s, args.kappa, args.uf)
+        vals.append(proj * 1e3)
+        expos.append(expo)
     v = statistics.median(vals)
     cb = {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-          "sample": f"oracle RGMRES-IR on randsvd n={n_s} per step, scaled by (n/{n_s})^3 to n={args.n}"}
+          "sample": f"oracle RGMRES-IR on randsvd at n={n_s // 2} and n={n_s} per step, projected to n={args.n} "
+                    f"with the fitted exponent (median {statistics.median(expos):.2f}); host CPU {cpu_model()}"}
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -290,17 +314,24 @@ def run_sweep(args, rank, world, local):
         xstar = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
         b = A @ xstar
         for uf in ("fp16", "bf16", "e4m3"):
-            for k in (args.k, 0):
-                prm = gir.Params(uf=uf, u="fp64", ur="fp64", m=args.m, k=k, tau=1e-8, imax=10, target_berr=1e-15,
-                                 carry_mode=1)
-                ms, ts, (x, info) = timed(solve_step(A, b, prm), args.steps, args.warmup)
+            # GCRO-DR(50, 10) against GMRES(50), and GCRO-DR(100, its_1 - 1) (the recycle dimension of
+            # Section 5, GIR_FLAG_ADAPTIVE_K) against GMRES(100); Arnoldi steps capped at 4 m per step
+            for m, k, adaptive in ((args.m, args.k, False), (args.m, 0, False), (100, 0, True), (100, 0, False)):
+                flags = gir.GIR_FLAG_ADAPTIVE_K if adaptive else 0
+                prm = gir.Params(uf=uf, u="fp64", ur="fp64", m=m, k=k, tau=1e-8, imax=10, target_berr=1e-15,
+                                 carry_mode=1, max_its=4 * m, flags=flags)
+                first = solve_step(A, b, prm)()
+                steps = args.steps if first[1].status == 0 else 1     # a stagnating run is timed once
+                ms, ts, (x, info) = timed(solve_step(A, b, prm), steps, 0)
                 ferr = ((x - xstar).abs().max() / xstar.abs().max()).item()
+                name = ("RGMRES-IR" if (k or adaptive) else "GMRES-IR") + f"(m={m}, k={'its_1-1' if adaptive else k})"
                 emit(sweep_line(args, world, f"randsvd dense n={n}, kappa_2={kappa:g}, b=A x*; u_f={uf}, u=u_r=fp64, "
-                                             f"{'RGMRES-IR' if k else 'GMRES-IR'}(m={args.m}, k={k}), tau=1e-8, "
-                                             f"target berr 1e-15",
-                                {"n": n, "kappa_2": kappa, "uf": uf, "u": "fp64", "ur": "fp64", "m": args.m, "k": k},
+                                             f"{name}, tau=1e-8, target berr 1e-15, <= {4 * m} Arnoldi steps per "
+                                             f"refinement step, i_max=10",
+                                {"n": n, "kappa_2": kappa, "uf": uf, "u": "fp64", "ur": "fp64", "m": m,
+                                 "k": "its_1-1" if adaptive else k, "max_its": 4 * m},
                                 ms, ts, {"status": info.status, "its": info.its, "total_its": info.total_its,
-                                         "ir_steps": info.ir_steps, "berr_dd": berr_dd(A, x, b),
+                                         "ir_steps": info.ir_steps, "k_eff": info.k_eff, "berr_dd": berr_dd(A, x, b),
                                          "ferr_vs_xstar": ferr, "ms_factor": info.ms_factor,
                                          "ms_solve": info.ms_solve}))
         # FP64 LU on the same GPU (cuSOLVER through torch), warm median
@@ -312,16 +343,18 @@ def run_sweep(args, rank, world, local):
         del A, b, xstar, xl
         torch.cuda.empty_cache()
 
-    # ---- prolate n=4096: (bf16, fp64, dd), GCRO-DR(30, k) with k = 10 against k = 0
-    np_ = 4096
-    for w in (0.25, 0.499):
-        A = torch.from_numpy(prolate(np_, w)).to(dev)
+    # ---- prolate: (bf16, fp64, dd), GCRO-DR(30, k) with k = 10 against k = 0; n = 4096 at w = 0.25
+    # (numerically singular) and 0.499, and at n = 4096 and 16384 with about ten eigenvalues near zero
+    # (w = 0.5 - 5 / n), where the recycle space carries the slow directions from step to step
+    from synth import prolate_torch
+    for np_, w in ((4096, 0.25), (4096, 0.499), (4096, 0.5 - 5.0 / 4096), (n, 0.5 - 5.0 / n)):
+        A = prolate_torch(np_, w, device=f"cuda:{local}")
         b = torch.from_numpy(rhs_uniform(np_, 0)).to(dev)
         for k in (10, 0):
             prm = gir.Params(uf="bf16", u="fp64", ur="dd", m=30, k=k, tau=1e-8, imax=10, target_berr=-1.0,
-                             carry_mode=1)
+                             carry_mode=1, max_its=120)
             ms, ts, (x, info) = timed(solve_step(A, b, prm), args.steps, args.warmup)
-            emit(sweep_line(args, world, f"prolate Toeplitz n={np_}, w={w}, b~U(0,1); u_f=bf16, u=fp64, u_r=dd; "
+            emit(sweep_line(args, world, f"prolate Toeplitz n={np_}, w={w:.7g}, b~U(0,1); u_f=bf16, u=fp64, u_r=dd; "
                                          f"GCRO-DR(30, {k}), tau=1e-8, target 2u",
                             {"n": np_, "w": w, "uf": "bf16", "u": "fp64", "ur": "dd", "m": 30, "k": k}, ms, ts,
                             {"status": info.status, "its": info.its, "total_its": info.total_its,
@@ -368,42 +401,33 @@ def run_sweep(args, rank, world, local):
         gg.manual_seed(5000 + i)
         As.append(A)
         bs.append(A @ torch.randn(nn, dtype=torch.float64, device=dev, generator=gg))
-    prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0, carry_mode=1)
-    ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm), max(1, args.steps // 2), 1)
+    prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0, carry_mode=1,
+                     max_its=4 * 30)
+    ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm), 1, 0)
     conv = sum(1 for i in infos if i.status == 0)
     emit(sweep_line(args, world, "batch of 512 randsvd systems, n~U{256..4096}, kappa_2=10^U(2,8), b=A x*; "
                                  "u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u",
-                    {"systems": 512, "n_total": int(sum(sizes)), "uf": "bf16", "m": 30, "k": 8}, ms, ts,
-                    {"status": st, "converged": conv, "total_its": int(sum(i.total_its for i in infos))},
+                    {"systems": 512, "n_total": int(sum(sizes)), "uf": "bf16", "m": 30, "k": 8, "max_its": 120}, ms, ts,
+                    {"status": st, "converged": conv, "total_its": int(sum(i.total_its for i in infos)),
+                     "converged_by_kappa": {f"1e{e}-1e{e + 1}": [sum(1 for i, kp in zip(infos, kappas)
+                                                                     if 10 ** e <= kp < 10 ** (e + 1) and i.status == 0),
+                                                                 sum(1 for kp in kappas if 10 ** e <= kp < 10 ** (e + 1))]
+                                            for e in range(2, 8)}},
                     metric="ms for the whole batch of 512 systems"))
     del As, bs, xs_
     torch.cuda.empty_cache()
 
     # ---- the oracle at two sizes (validates the n^3 projection of the headline's cpu_baseline)
     if rank == 0 and not args.no_cpu:
-        pts = []
-        for n_s in (1536, 3072):
-            dt, info = oracle_sample(n_s, args.kappa, args.uf)
-            pts.append((n_s, dt, info.paper_format()))
-        (n1, t1, _), (n2, t2, _) = pts
-        expo = np.log(t2 / t1) / np.log(n2 / n1)
+        proj, t1, t2, expo, i1, i2 = oracle_projection(args.n, args.sample_n, args.kappa, args.uf)
+        n1, n2 = args.sample_n // 2, args.sample_n
+        pts = [(n1, t1, i1.paper_format()), (n2, t2, i2.paper_format())]
         emit({"metric": "oracle seconds (CPU) on randsvd kappa_2=1e2 at two sizes", "sweep": True,
               "value": t2, "unit": "s", "cpu_baseline": {"value": t2 * 1e3, "unit": "ms", "cores": os.cpu_count(),
                                                           "kind": "oracle", "sample": f"n={n2}"},
               "result": {"points": [{"n": a, "s": b, "its": c} for a, b, c in pts], "fitted_exponent": expo,
                          "projected_ms_n16384": t2 * 1e3 * (args.n / n2) ** expo, "cpu": cpu_model()}})
     return 0
-
-
-def cpu_model():
-    try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part", "hardware")):
-                return line.split(":", 1)[1].strip()
-    except OSError:
-        pass
-    import platform
-    return platform.processor() or platform.machine()
 
 
 def main():
@@ -421,6 +445,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-lu", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="the measurement matrix instead of the headline: kappa_2 x u_f with the k = 0 comparator, "
                          "the FP64 LU comparator, prolate n=4096 recycling counts, conv-diff n=10000 forward + "
@@ -460,6 +485,12 @@ def main():
         _, info = F.solve(Ad, bd, x)
         F.close()
         return info
+
+    def step_x(Ad, bd, p):
+        F = gir.Factorization(Ad, p)
+        xx, info = F.solve(Ad, bd)
+        F.close()
+        return xx, info
 
     x = torch.empty_like(b)
     for _ in range(args.warmup):
@@ -527,18 +558,54 @@ def main():
                "d2h_bytes_per_step": 8 * n, "api": "paper_2201_09827_gb300.solve(A_host_pinned, b_host_pinned)"}
         del Ah, bh
 
-    # ---------------- FP64 LU comparator on the same GPU (library, context) ----------------
+    # ---------------- comparators on the same GPU ----------------
+    def timed_steps(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts, res = [], None
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), res
+
+    comparators = {}
     fp64_lu_ms = None
     if not args.no_fp64_lu and rank == 0:
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        xl = torch.linalg.solve(A, b)
-        e1.record(stream)
-        e1.synchronize()
-        fp64_lu_ms = e0.elapsed_time(e1)
+        # FP64 LU solve (cuSOLVER getrf/getrs through torch), warm median of 3
+        fp64_lu_ms, xl = timed_steps(lambda: torch.linalg.solve(A, b), 3, 1)
+        comparators["fp64_lu"] = {"ms": fp64_lu_ms, "api": "torch.linalg.solve (cuSOLVER), warm median of 3"}
         del xl
+    if rank == 0 and not args.no_comparators:
+        # GMRES-IR (k = 0) on the same system
+        prm0 = gir.Params(uf=args.uf, u="fp64", ur="fp64", m=args.m, k=0, tau=1e-8, imax=10, target_berr=1e-15,
+                          carry_mode=1)
+        ms0, (_, i0) = timed_steps(lambda: step_x(A, b, prm0), 3, 1)
+        comparators["gmres_ir_same_system"] = {"ms": ms0, "its": i0.its, "total_its": i0.total_its,
+                                               "status": i0.status, "m": args.m, "k": 0}
+        # recycling where the preconditioned operator has a few outlying eigenvalues: prolate
+        # Toeplitz with about ten eigenvalues near zero (w = 0.5 - 5/n), (bf16, fp64, dd), m = 30
+        from synth import prolate_torch
+        wp = 0.5 - 5.0 / n
+        Ap = prolate_torch(n, wp, device=f"cuda:{local}")
+        gp = torch.Generator(device=dev)
+        gp.manual_seed(0)
+        bp = torch.rand(n, dtype=torch.float64, device=dev, generator=gp)
+        rec = {"workload": f"prolate Toeplitz n={n}, w=0.5-5/n={wp:.7f}, b~U(0,1); u_f=bf16, u=fp64, u_r=dd, "
+                           f"m=30, tau=1e-8, target 2u"}
+        for kk in (10, 0):
+            prm_p = gir.Params(uf="bf16", u="fp64", ur="dd", m=30, k=kk, tau=1e-8, imax=10, target_berr=-1.0,
+                               carry_mode=1, max_its=120)
+            msp, (_, ip) = timed_steps(lambda: step_x(Ap, bp, prm_p), 3, 1)
+            rec[f"k{kk}"] = {"ms": msp, "its": ip.its, "total_its": ip.total_its, "status": ip.status}
+        comparators["prolate_recycling"] = rec
+        del Ap, bp
+        torch.cuda.empty_cache()
 
     # ---------------- roofline of the dominant kernel ----------------
     # Phases are kernel launches timed by CUDA events on their own streams inside the library;
@@ -567,7 +634,8 @@ def main():
                "result": {"status": last.status, "its": last.its, "total_its": last.total_its,
                           "ir_steps": last.ir_steps, "berr_dd": eta, "ms_factor": last.ms_factor,
                           "ms_solve": last.ms_solve, "times_ms": times},
-               "fp64_lu_ms": fp64_lu_ms, "phase_ms_per_step": phase_ms, "roofline_next": others,
+               "fp64_lu_ms": fp64_lu_ms, "comparators": comparators, "phase_ms_per_step": phase_ms,
+               "roofline_next": others,
                "timing_note": ("roofline kernels timed by CUDA events inside the timed region (phases "
                                + ", ".join(ROOFLINE_PHASES) + "); phase_ms_per_step from one extra "
                                "step after it with every phase timed")}

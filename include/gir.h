@@ -137,8 +137,10 @@ gir_status gir_solve(gir_handle* h, const double* A, int64_t lda, const double* 
 
 /* Adjoint solve A^T lambda = g by the same refinement, left-preconditioned with M^T
  * (operator M^-T A^T), reusing the factors of gir_factor. Keeps its own recycle space,
- * seeded from the forward U_k when the adjoint one is empty. Not in the paper (used for
- * gradients: db = lambda, dA = -lambda x^T). Same arguments and statuses as gir_solve. */
+ * seeded from the forward U_k when the adjoint one is empty. The residual g - A^T lambda is
+ * computed in the handle's u_r (FP64, or double-double: exact products, dd sums). Not in the
+ * paper (used for gradients: db = lambda, dA = -lambda x^T). Same arguments and statuses as
+ * gir_solve. */
 gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const double* g,
                              double* lambda, gir_info* info, void* stream);
 

@@ -84,6 +84,7 @@ struct gir_handle {
     float ms_factor = 0.f;   // device time of the factorization, reported in every gir_info
     bool dd = false;         // u_a = double-double (the paper's u^2 for u = FP64)
     DdState ddst;            // buffers of the double-double operator
+    double2* respart = nullptr;  // partial sums of the adjoint's double-double residual (u_r = dd, u_a != dd)
     int k_run = 0;           // recycle dimension in use (params k, or its_1 - 1 with GIR_FLAG_ADAPTIVE_K)
     bool k_open = false;     // GIR_FLAG_ADAPTIVE_K: k is fixed by the next first GMRES cycle
     SmallState* hst = nullptr;  // pinned host mirror of the SmallState header
@@ -146,7 +147,7 @@ void free_handle_on(gir_handle* h, cudaStream_t s) {
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
                     h->scratch, h->st, h->qh, h->dsc, h->dflags, h->Ahi, h->Alo, h->vsplit,
                     h->ddst.DL, h->ddst.DU, h->ddst.z, h->ddst.y1, h->ddst.y2, h->ddst.w, h->ddst.part,
-                    h->ddst.ready};
+                    h->ddst.ready, h->respart};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, s);
     if (h->hsc) cudaFreeHost(h->hsc);
@@ -543,6 +544,8 @@ gir_status refine(gir_handle* h, const double* A, int64_t lda, const double* b, 
         { int tslot_ = trace_begin(s, "residual");
         if (!trans) {
             GIR_TRY(launch_residual(A, n, lda, x, b, h->rr, h->p.ur == GIR_DD, s, cw ? h->dsc + SC_OMEGA : nullptr));
+        } else if (h->p.ur == GIR_DD) {
+            GIR_TRY(residual_t_dd(A, n, lda, x, b, h->rr, h->dd ? h->ddst.part : h->respart, s));
         } else {
             GIR_TRY(launch_gemv(A, n, lda, x, h->vtmp, 1, h->scratch, s));
             count_launch(), k_sub<<<grid1(n), 256, 0, s>>>(b, h->vtmp, h->rr, n);
@@ -721,6 +724,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
         ALLOC(h->Alo, (size_t)n * h->ldf);
         ALLOC(h->vsplit, (size_t)2 * h->ldf);
     }
+    if (params->ur == GIR_DD && !h->dd) ALLOC(h->respart, dd_part_len(n));
     ALLOC(h->r, n);
     ALLOC(h->dvec, n);
     ALLOC(h->cvec, n);

@@ -145,7 +145,33 @@ __global__ void k_sum_parts_dd(const double2* __restrict__ part, int nparts, int
     }
 }
 
+// r_j = fl64(b_j - sum_c part[c][j]): the transposed residual with A^T x summed in double-double
+// (the residual of the adjoint solve in u_r = double-double), one rounding at the end
+__global__ void k_resid_t_dd(const double2* __restrict__ part, int nparts, int64_t n, const double* __restrict__ b,
+                             double* __restrict__ r) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double sh = 0.0, sl = 0.0;
+        for (int c = 0; c < nparts; ++c) {
+            const double2 p = part[(int64_t)c * n + j];
+            dd_acc(sh, sl, p.x, p.y);
+        }
+        double rh, rl;
+        two_sum(b[j], -sh, rh, rl);
+        r[j] = rh + (rl - sl);
+    }
+}
+
 size_t dd_part_len(int64_t n) { return (size_t)((n + DD_TROWS - 1) / DD_TROWS) * (size_t)n; }
+
+gir_status residual_t_dd(const double* A, int64_t n, int64_t lda, const double* x, const double* b, double* r,
+                         double2* part, cudaStream_t s) {
+    const dim3 grid((unsigned)((n + 255) / 256), (unsigned)((n + DD_TROWS - 1) / DD_TROWS));
+    count_launch(), k_gemv_t_dd_partial<<<grid, 256, 0, s>>>(A, n, lda, x, part);
+    count_launch(), k_resid_t_dd<<<(unsigned)gmin<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(part, (int)grid.y, n,
+                                                                                               b, r);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
 
 static int rows_grid(int64_t n) { return (int)gmax<int64_t>(1, gmin<int64_t>((n + 7) / 8, 152 * 16)); }
 

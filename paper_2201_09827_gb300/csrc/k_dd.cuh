@@ -24,6 +24,10 @@ struct DdState {
 };
 
 size_t dd_part_len(int64_t n);
+// r = fl64(b - A^T x) with exact products and double-double sums (the adjoint residual in
+// u_r = double-double); part: dd_part_len(n) double2 of scratch.
+gir_status residual_t_dd(const double* A, int64_t n, int64_t lda, const double* x, const double* b, double* r,
+                         double2* part, cudaStream_t s);
 // Diagonal-block inverses of L and U in double-double (once per factorization).
 gir_status dd_setup(DdState& dd, const TrsvState& st, cudaStream_t s);
 // w = A v (trans = 0) or A^T v (trans = 1) with exact products and double-double sums.

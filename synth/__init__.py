@@ -11,6 +11,7 @@ from .generators import (  # noqa: F401
     randsvd,
     randsvd_torch,
     prolate,
+    prolate_torch,
     convdiff,
     rhs_uniform,
     normal_vector,

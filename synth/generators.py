@@ -81,6 +81,23 @@ def prolate(n: int, w: float) -> np.ndarray:
     return col[idx]
 
 
+def prolate_torch(n: int, w: float, device: str = "cuda"):
+    """Prolate Toeplitz matrix built on ``device`` (FP64 torch tensor, same entries as ``prolate``)."""
+    import torch
+
+    j = np.arange(1, n, dtype=np.float64)
+    col = np.empty(n)
+    col[0] = 2.0 * w
+    col[1:] = np.sin(2.0 * np.pi * w * j) / (np.pi * j)
+    c = torch.from_numpy(col).to(device)
+    idx = torch.arange(n, device=device)
+    a = torch.empty(n, n, dtype=torch.float64, device=device)
+    for r0 in range(0, n, 1024):
+        r1 = min(n, r0 + 1024)
+        a[r0:r1] = c[(idx[r0:r1, None] - idx[None, :]).abs()]
+    return a
+
+
 def convdiff(N: int = 100, peclet: float = 50.0) -> np.ndarray:
     """Dense FP64 matrix of -Lap(u) + beta.grad(u) on an N x N interior grid of the unit square.
 

@@ -163,11 +163,14 @@ def test_factor_properties(G, n, fmt):
     F.close()
 
 
-@pytest.mark.parametrize("n,fmt", [(64, "bf16"), (300, "fp16"), (1000, "bf16"), (1031, "fp16")])
+@pytest.mark.parametrize("n,fmt", [(64, "bf16"), (300, "fp16"), (1000, "bf16"), (1031, "fp16"), (1537, "bf16"),
+                                   (2600, "fp16"), (4096, "bf16")])
 def test_apply_minv_and_atilde(G, n, fmt):
     """With the same (GPU) factors, M^-1 v and M^-1 A v agree with the oracle's FP64 substitution
     to the float-float accuracy of the triangular solves: about 2^-46 per operation, amplified
-    by the conditioning of the factors (kappa_2(A) = 1e4 here), so 1e-14 * kappa relative."""
+    by the conditioning of the factors (kappa_2(A) = 1e4 here), so 1e-14 * kappa relative.
+    n = 1537, 2600 and 4096 span several 16-CTA clusters of 64-row blocks (1024 rows each), the
+    first two with a ragged last block."""
     kappa = 1e4
     A = randsvd(n, kappa, seed=7)
     F, Fg = _gpu_factors(G, A, fmt)

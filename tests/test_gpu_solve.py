@@ -332,6 +332,73 @@ def test_adjoint_matches_oracle(pkg):
     assert abs(info.total_its - io.total) <= 0.1 * io.total + 1
 
 
+def test_adjoint_dd_residual_matches_oracle(pkg):
+    """The adjoint solve with u_r = double-double (its residual g - A^T lambda from exact products
+    and dd sums) against the oracle's transposed solve with the same triple (bf16, fp64, dd) on a
+    prolate matrix, each side on its own factors: same status, iterations within 10%, backward error
+    of the transposed system within 4x of the oracle's, and below the FP64 target."""
+    n = 600
+    A = prolate(n, 0.495)
+    g = rhs_uniform(n, 7)
+    prm = pkg.Params(uf="bf16", u="fp64", ur="dd", m=30, k=10, tau=1e-8, target_berr=1e-15)
+    F = pkg.Factorization(cuda(A), prm)
+    lam, info = F.solve_adjoint(cuda(A), cuda(g))
+    F.close()
+    lam = lam.cpu().numpy()
+    lo, io, _, _ = osolve(A, g, OP(uf="bf16", u="fp64", ur="dd", ua="u", m=30, k=10, tau=1e-8, target=1e-15,
+                                   lu_w=32), transpose=True)
+    assert info.status == 0 and io.converged
+    be, beo = normwise_berr(A.T, lam, g), normwise_berr(A.T, lo, g)
+    assert be <= 4 * max(beo, UNIT_ROUNDOFF["fp64"]) and be <= 1e-15
+    assert abs(info.total_its - io.total) <= 0.1 * io.total + 1
+    assert_forward_error(A.T, g, lam, "fp64", "dd", lo)
+
+
+def test_gradients_convdiff_n2500(pkg):
+    """Gradients of L = ||x - x_t||^2 through the differentiable solve on the dense conv-diff
+    operator (N = 50, n = 2500, Pe = 50; BF16 LU, RGMRES-IR(40, 10)): db and dA against the
+    oracle's FP64 gradient (relative 1e-8) and against central finite differences of the GPU
+    solve (h = 1e-6, relative 1e-5) on sampled entries."""
+    from oracle.ir import adjoint_gradients
+    N = 50
+    n = N * N
+    A = convdiff(N, 50.0)
+    b = rhs_uniform(n, 4)
+    xt = normal_vector(n, 5)
+    prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=40, k=10, tau=1e-8, target_berr=1e-15)
+    Ad = cuda(A).requires_grad_(True)
+    bd = cuda(b).requires_grad_(True)
+    x = pkg.GirSolve.apply(Ad, bd, prm)
+    loss = ((x - cuda(xt)) ** 2).sum()
+    loss.backward()
+    db = bd.grad.cpu().numpy()
+    dA = Ad.grad.cpu().numpy()
+    op = OP(uf="bf16", u="fp64", ur="fp64", ua="u", m=40, k=10, tau=1e-8, target=1e-15, lu_w=32)
+    xo, io, _, _ = osolve(A, b, op)
+    lam_o, dA_o, _ = adjoint_gradients(A, b, xo, 2 * (xo - xt), op)
+    assert np.abs(db - lam_o).max() <= 1e-8 * np.abs(lam_o).max()
+    assert np.abs(dA - dA_o).max() <= 1e-8 * np.abs(dA_o).max()
+    h = 1e-6
+
+    def L(Am, bm):
+        F = pkg.Factorization(cuda(Am), prm)
+        xx, _ = F.solve(cuda(Am), cuda(bm))
+        F.close()
+        return float(((xx.cpu().numpy() - xt) ** 2).sum())
+
+    for (i, j) in [(0, 0), (1234, 1235), (2499, 2449)]:
+        Ap, Am = A.copy(), A.copy()
+        Ap[i, j] += h
+        Am[i, j] -= h
+        fd = (L(Ap, b) - L(Am, b)) / (2 * h)
+        assert abs(fd - dA[i, j]) <= 1e-5 * max(1.0, abs(fd))
+    bp, bm = b.copy(), b.copy()
+    bp[777] += h
+    bm[777] -= h
+    fd = (L(A, bp) - L(A, bm)) / (2 * h)
+    assert abs(fd - db[777]) <= 1e-5 * max(1.0, abs(fd))
+
+
 def test_batch_uneven(pkg):
     """Uneven orders in one batch (BF16 u_f, kappa_2 1e2 and 1e3, where both the oracle and the GPU
     converge robustly; with kappa_2 * u_f >> 1 the outcome of either depends on rounding noise):
