@@ -97,6 +97,12 @@ typedef struct {
  * |theta| values within about 1e-6 relative of each other straddle the k-th place. The FP64
  * iteration takes several times longer on GB300 (its dependent FP64 chains). */
 #define GIR_FLAG_EIG_FP64 0x10u
+/* Low-precision basis storage inside GCRO-DR (Section 5 names mixed precision within the
+ * recycling solver as future work): the Arnoldi vectors v_j and the recycle vectors C_k, U_k are
+ * rounded to FP32 when they are formed; the vector being orthogonalised, d, r and all inner
+ * products stay in u. The vectors are still held in FP64 arrays (the numerics of FP32 storage;
+ * the halved basis traffic is not built). */
+#define GIR_FLAG_BASIS_FP32 0x20u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64

@@ -36,6 +36,12 @@ Readings where the paper is silent or garbled:
   below 1e-12 max |R_jj| are dropped (the recycle dimension shrinks).
 * Vectors are stored in precision u (rounded after each vector operation); inner products,
   norms and all small dense algebra (least squares, eigenproblems, QR) are FP64.
+
+Low-precision basis storage (the mixed precision inside GCRO-DR that Section 5 names as future
+work): with ``basis`` set to a format, every stored basis vector -- the Arnoldi vectors v_j and
+the recycle vectors C_k and U_k -- is rounded to that format when it is formed, while the
+working vectors (the vector being orthogonalised, d and r) stay in u. ``basis=None`` stores
+them in u.
 """
 from __future__ import annotations
 
@@ -140,19 +146,22 @@ def _givens_estimate(H, j, g, cs, sn):
     return abs(g[j + 1])
 
 
-def arnoldi(op, r, C, steps, tol, u):
+def arnoldi(op, r, C, steps, tol, u, store=None):
     """Up to ``steps`` Arnoldi steps of (I - C C^T) A~ from v1 = r/||r|| with CGS2.
 
-    Returns V (n x (j+1)), H ((j+1) x j), B (kc x j), j, Givens estimates.
+    The basis vectors are stored in precision ``store`` (default: u). Returns V (n x (j+1)),
+    H ((j+1) x j), B (kc x j), j, Givens estimates.
     """
     fu = (lambda z: round_to(z, u))
+    fmt_v = store or u
+    fb = (lambda z: round_to(z, fmt_v))
     n = r.shape[0]
     kc = C.shape[1]
     beta = np.linalg.norm(r)
     V = np.zeros((n, steps + 1))
     H = np.zeros((steps + 1, steps))
     B = np.zeros((kc, steps))
-    V[:, 0] = fu(r / beta)
+    V[:, 0] = fb(r / beta)
     g = np.zeros(steps + 1)
     g[0] = beta
     cs = np.zeros(steps)
@@ -170,7 +179,7 @@ def arnoldi(op, r, C, steps, tol, u):
         h = np.linalg.norm(w)
         H[j + 1, j] = h
         if h > 0.0:
-            V[:, j + 1] = fu(w / h)
+            V[:, j + 1] = fb(w / h)
         e = _givens_estimate(H, j, g, cs, sn)
         est.append(e)
         j += 1
@@ -185,7 +194,7 @@ def _lstsq(G, rhs):
     return sla.solve_triangular(R, Q.T @ rhs, lower=False)
 
 
-def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_auto=None):
+def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_auto=None, basis=None):
     """Solve A~ d = c by GCRO-DR(m, k) from d0 = 0.
 
     op:     v -> A~ v (already rounded to u).
@@ -196,9 +205,13 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_au
     k_auto: None, or a cap k_max: when the first (GMRES) cycle converges after j steps, the
             recycle dimension becomes min(j - 1, k_max) -- Section 5's observation that recycling
             the whole first-step subspace, k = its_1 - 1, gives the fewest iterations.
+    basis:  None (basis vectors stored in u) or the format in which the Arnoldi vectors and the
+            recycle vectors C, U are stored (low-precision basis storage, Section 5).
     Returns d, U (the Y~ for the next system), C, info (info.k_used: the k that was used).
     """
     fu = (lambda z: round_to(z, u))
+    fmt_b = basis or u
+    fb = (lambda z: round_to(z, fmt_b))
     c = np.asarray(c, dtype=np.float64)
     n = c.shape[0]
     info = GcroInfo()
@@ -222,12 +235,12 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_au
         Z = np.stack([op(Ytil[:, i]) for i in range(Ytil.shape[1])], axis=1)
         info.carry_applies = Ytil.shape[1]
         Q, R, keep = _qr_pos(Z)
-        C = fu(Q)
-        U = fu(sla.solve_triangular(R, Ytil[:, keep].T, trans="T", lower=False).T)
+        C = fb(Q)
+        U = fb(sla.solve_triangular(R, Ytil[:, keep].T, trans="T", lower=False).T)
         d = fu(d + U @ (C.T @ r))
         r = fu(r - C @ (C.T @ r))
     else:
-        V, H, _, j, est = arnoldi(op, r, np.zeros((n, 0)), m, tol, u)
+        V, H, _, j, est = arnoldi(op, r, np.zeros((n, 0)), m, tol, u, basis)
         info.its += j
         info.cycles += 1
         info.resid += est
@@ -252,13 +265,13 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_au
             if P.shape[1] > 0:
                 Y = V[:, :j] @ P
                 Q, R, keep = _qr_pos(H @ P)
-                C = fu(V @ Q)
-                U = fu(sla.solve_triangular(R, Y[:, keep].T, trans="T", lower=False).T)
+                C = fb(V @ Q)
+                U = fb(sla.solve_triangular(R, Y[:, keep].T, trans="T", lower=False).T)
 
     while np.linalg.norm(r) > tol and info.its < max_its:
         kc = C.shape[1]
         steps = max(1, min(m - kc, max_its - info.its))
-        V, H, B, j, est = arnoldi(op, r, C, steps, tol, u)
+        V, H, B, j, est = arnoldi(op, r, C, steps, tol, u, basis)
         info.its += j
         info.cycles += 1
         info.resid += est
@@ -283,8 +296,8 @@ def gcrodr(op, c, m, k, tau, Ytil=None, u="fp64", max_its=None, carry=None, k_au
             P = select_harmonic(theta, Zv, k, kc + j, m)
             if P.shape[1] > 0:
                 Q, R, keep = _qr_pos(G @ P)
-                C = fu(What @ Q)
-                U = fu(sla.solve_triangular(R, (Vhat @ P)[:, keep].T, trans="T", lower=False).T)
+                C = fb(What @ Q)
+                U = fb(sla.solve_triangular(R, (Vhat @ P)[:, keep].T, trans="T", lower=False).T)
     info.converged = bool(np.linalg.norm(r) <= tol)
     info.k_eff = U.shape[1]
     info.k_used = k

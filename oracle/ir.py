@@ -61,6 +61,7 @@ class Params:
     lu_mode: str = "block"        # 'block' or 'chop'
     lu_w: int = 64
     max_its: int | None = None    # Arnoldi steps per GCRO-DR call
+    basis: str | None = None      # storage format of the Krylov and recycle basis vectors (None: u)
 
 
 @dataclass
@@ -204,6 +205,7 @@ def solve(A, b, p: Params, F=None, xstar=None, transpose=False, Y0=None):
         c = minv(rhat)
         auto = p.k_max if (p.k_mode == "knee" and kk is None) else None
         d, U, C, gi = gcrodr(op, c, p.m, p.k if kk is None else kk, p.tau, Ytil=Y, u=p.u, max_its=p.max_its,
+                             basis=p.basis,
                              carry=carry, k_auto=auto)
         if kk is None and p.k_mode == "knee":
             kk = gi.k_used

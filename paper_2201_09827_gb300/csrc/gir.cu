@@ -43,6 +43,7 @@ struct gir_handle {
     gir_params p{};
     int fmt = FF_BF16;
     int round32 = 0;
+    int rbasis = 0;          // store the Krylov and recycle basis vectors rounded to FP32 (u = FP32 or GIR_FLAG_BASIS_FP32)
     int dev = 0;
     // factors
     uint16_t* LU = nullptr;
@@ -178,7 +179,8 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->k < 0 || p->k >= p->m || p->k > GIR_MAX_K) return GIR_INVALID_ARG;
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
-    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR | GIR_FLAG_ADAPTIVE_K | GIR_FLAG_EIG_FP64)) != 0)
+    if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR | GIR_FLAG_ADAPTIVE_K | GIR_FLAG_EIG_FP64 |
+                      GIR_FLAG_BASIS_FP32)) != 0)
         return GIR_INVALID_ARG;
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;
@@ -329,7 +331,7 @@ gir_status arnoldi_step(gir_handle* h, const double* A, int64_t lda, int trans, 
     GIR_TRY(launch_gemm_nn(basis, h->ldb, p, ST_PTR(h, s2), p, 1, w, h->ldb, -1.0, 1.0, n, h->round32, s));
     GIR_TRY(launch_norm2(w, n, ST_PTR(h, hnorm), h->scratch, s));
     GIR_TRY(launch_givens_step(h->st, s));
-    GIR_TRY(launch_scale_by(w, n, ST_PTR(h, hnorm), 1, h->round32, s));
+    GIR_TRY(launch_scale_by(w, n, ST_PTR(h, hnorm), 1, h->rbasis, s));
     trace_end(tslot_, "cgs2+givens", s); }
     return GIR_OK;
 }
@@ -339,7 +341,7 @@ gir_status run_cycle(gir_handle* h, const double* A, int64_t lda, int trans, int
                      int* taken, cudaStream_t s) {
     // v_1 = r / ||r||  (||r|| is in dsc[SC_NRM2])
     GIR_CUDA_TRY(cudaMemcpyAsync(V(h, 0), h->r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    GIR_TRY(launch_scale_by(V(h, 0), h->n, h->dsc + SC_NRM2, 1, h->round32, s));
+    GIR_TRY(launch_scale_by(V(h, 0), h->n, h->dsc + SC_NRM2, 1, h->rbasis, s));
     count_launch(), k_cycle_init<<<1, 32, 0, s>>>(h->st, h->dsc + SC_NRM2, tol, kc, first, h->k_run, h->p.m,
                                                    (h->p.flags & GIR_FLAG_EIG_FP64) ? 1 : 0);
     int j = 0;
@@ -363,6 +365,7 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
     int k = h->k_run;
     const int max_its = h->p.max_its > 0 ? h->p.max_its : 20 * m;
     const int r32 = h->round32;
+    const int rb = h->rbasis;   // rounding of stored basis vectors (C, U, V)
     int its = 0;
     *carry_applies = 0;
     GIR_TRY(launch_norm2(c, n, h->dsc + SC_NRM2, h->scratch, s));
@@ -396,8 +399,8 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
             GIR_TRY(read_header(h, s));
             if (h->hst->knew == kc) {
                 GIR_TRY(launch_gemm_nn(h->Utmp, n, kc, ST_PTR(h, Ccoef), SM_LDG, kc, Cregion(h, kc), h->ldb, 1.0, 0.0,
-                                       n, r32, s));
-                GIR_TRY(launch_gemm_nn(h->Ucur, n, kc, ST_PTR(h, Rinv), SM_KMAX, kc, h->Utmp, n, 1.0, 0.0, n, r32, s));
+                                       n, rb, s));
+                GIR_TRY(launch_gemm_nn(h->Ucur, n, kc, ST_PTR(h, Rinv), SM_KMAX, kc, h->Utmp, n, 1.0, 0.0, n, rb, s));
                 GIR_CUDA_TRY(
                     cudaMemcpyAsync(h->Ucur, h->Utmp, (size_t)kc * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
             } else {
@@ -438,8 +441,8 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
         const int knew = h->hst->knew;
         if (knew > 0) {
             GIR_TRY(launch_gemm_nn(V(h, 0), h->ldb, j + 1, ST_PTR(h, Ccoef), SM_LDG, knew, Cregion(h, knew), h->ldb,
-                                   1.0, 0.0, n, r32, s));
-            GIR_TRY(launch_gemm_nn(V(h, 0), h->ldb, j, ST_PTR(h, Ucoef), SM_LDG, knew, h->Ucur, n, 1.0, 0.0, n, r32, s));
+                                   1.0, 0.0, n, rb, s));
+            GIR_TRY(launch_gemm_nn(V(h, 0), h->ldb, j, ST_PTR(h, Ucoef), SM_LDG, knew, h->Ucur, n, 1.0, 0.0, n, rb, s));
         }
         kc = knew;
     }
@@ -473,12 +476,12 @@ gir_status gcrodr(gir_handle* h, const double* A, int64_t lda, int trans, Recycl
         if (knew > 0) {
             // C_new = [C V_{j+1}] Ccoef -> Ctmp ; U_new = U Ucoef_top + V_j Ucoef_bot -> Utmp
             GIR_TRY(launch_gemm_nn(Cregion(h, kc), h->ldb, kc + j + 1, ST_PTR(h, Ccoef), SM_LDG, knew, h->Ctmp, n, 1.0,
-                                   0.0, n, r32, s));
+                                   0.0, n, rb, s));
             GIR_TRY(launch_gemm_nn(V(h, 0), h->ldb, j, ST_PTR(h, Ucoef) + kc, SM_LDG, knew, h->Utmp, n, 1.0, 0.0, n, 0,
                                    s));
             if (kc > 0)
                 GIR_TRY(launch_gemm_nn(h->Ucur, n, kc, ST_PTR(h, Ucoef), SM_LDG, knew, h->Utmp, n, 1.0, 1.0, n, 0, s));
-            if (r32) count_launch(), k_round32<<<grid1((int64_t)knew * n), 256, 0, s>>>(h->Utmp, (int64_t)knew * n);
+            if (rb) count_launch(), k_round32<<<grid1((int64_t)knew * n), 256, 0, s>>>(h->Utmp, (int64_t)knew * n);
             GIR_CUDA_TRY(cudaMemcpyAsync(Cregion(h, knew), h->Ctmp, (size_t)knew * n * sizeof(double),
                                          cudaMemcpyDeviceToDevice, s));
             GIR_CUDA_TRY(
@@ -669,6 +672,7 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     h->k_open = (params->flags & GIR_FLAG_ADAPTIVE_K) != 0;
     h->fmt = (params->uf == GIR_FP16) ? FF_FP16 : FF_BF16;
     h->round32 = (params->u == GIR_FP32);
+    h->rbasis = h->round32 || (params->flags & GIR_FLAG_BASIS_FP32) != 0;
     h->scaled = (params->uf == GIR_FP16);
     h->dd = (params->ua == GIR_DD);
     cudaGetDevice(&h->dev);

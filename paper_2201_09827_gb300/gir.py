@@ -139,6 +139,7 @@ GIR_FLAG_CW_BERR = 0x2   # also compute the componentwise backward error and sto
 GIR_FLAG_SIR = 0x4       # Algorithm 1 comparator: correction by substitution, no GCRO-DR
 GIR_FLAG_ADAPTIVE_K = 0x8  # k = its_1 - 1 from the first refinement step (Section 5)
 GIR_FLAG_EIG_FP64 = 0x10  # harmonic Ritz eigenvalues by FP64 Hessenberg QR (default FP32)
+GIR_FLAG_BASIS_FP32 = 0x20  # Krylov and recycle basis vectors rounded to FP32 when stored
 
 
 @dataclass

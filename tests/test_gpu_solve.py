@@ -40,7 +40,7 @@ def gpu_factors_for_oracle(F, n, uf):
 
 
 def run_both(pkg, A, b, uf, u, ur, m, k, tau, imax=10, target=None, max_its=None, carry=1, same_factors=False,
-             flags=0, solver="gcrodr", stop="berr", k_mode="fixed", ua_dd=False):
+             flags=0, solver="gcrodr", stop="berr", k_mode="fixed", ua_dd=False, basis=None):
     """GPU solve and oracle solve. same_factors=True gives the oracle the GPU's u_f factors, which
     isolates the refinement/GCRO-DR part for problems whose iteration counts are sensitive to the
     FP32 summation order of the factorization (poor preconditioners, kappa * u_f >> 1)."""
@@ -54,7 +54,8 @@ def run_both(pkg, A, b, uf, u, ur, m, k, tau, imax=10, target=None, max_its=None
     F.close()
     op = OP(uf=uf, u=u, ur=ur, ua="u2" if (ua_dd or u != "fp64") else "u", m=m, k=k, tau=tau, imax=imax,
             target=target,
-            lu_w=32, max_its=max_its or 20 * m, carry_mode=carry, solver=solver, stop=stop, k_mode=k_mode)
+            lu_w=32, max_its=max_its or 20 * m, carry_mode=carry, solver=solver, stop=stop, k_mode=k_mode,
+            basis=basis)
     xo, io, _, _ = osolve(A, b, op, F=Fo)
     return x, info, xo, io
 
@@ -628,6 +629,30 @@ def test_dd_operator_solve_parity(pkg, case):
                                    same_factors=True, ua_dd=True)
     assert info.status == 0 and io.converged
     assert_parity(A, b, x, info, xo, io, "fp64", ur="dd" if case == "prolate" else "fp64")
+
+
+def test_fp32_basis_storage_parity(pkg):
+    """GIR_FLAG_BASIS_FP32 (the Krylov and recycle basis vectors rounded to FP32 when stored) against
+    the oracle's basis='fp32' mode on the same factors. On a randsvd system it costs about one
+    iteration and still reaches 1e-15 (oracle: 43 (21,22) against 42 (21,21) with FP64 storage).
+    On prolate (w = 0.495, u_r = dd) both stagnate near eta = 1e-8: the FP32-stored basis puts an
+    error of order u_32 into every correction, which the refinement cannot remove."""
+    from paper_2201_09827_gb300 import gir
+    n = 1024
+    A = randsvd(n, 1e3, seed=0)
+    b = A @ normal_vector(n, 2)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "fp64", 30, 10, 1e-8, target=1e-15, same_factors=True,
+                               flags=gir.GIR_FLAG_BASIS_FP32, basis="fp32")
+    assert info.status == 0 and io.converged
+    assert_parity(A, b, x, info, xo, io, "fp64")
+    A = prolate(n, 0.495)
+    b = rhs_uniform(n, 0)
+    x, info, xo, io = run_both(pkg, A, b, "bf16", "fp64", "dd", 30, 10, 1e-8, imax=6, max_its=300,
+                               same_factors=True, flags=gir.GIR_FLAG_BASIS_FP32, basis="fp32")
+    assert info.status == gir.GIR_NOT_CONVERGED and not io.converged
+    be, beo = normwise_berr(A, x, b), normwise_berr(A, xo, b)
+    assert 1e-10 < be < 1e-6 and 1e-10 < beo < 1e-6
+    assert be <= 10 * beo and beo <= 10 * be
 
 
 def test_bounded_wait_times_out_and_context_survives(pkg):

@@ -195,3 +195,58 @@ def test_recycling_reduces_second_solve():
     # carrying (U, C) instead of recomputing QR(A~ Y~) gives the same solve
     _, _, _, i2c = G.gcrodr(op, c2, 16, 4, 1e-8, carry=(U, C))
     assert abs(i2c.its - i2.its) <= 1 and i2c.carry_applies == 0 and i2.carry_applies == U.shape[1]
+
+
+U32 = 2.0 ** -24
+
+
+def test_fp32_basis_storage_relation_and_rounding():
+    """Low-precision basis storage (Section 5's future work): with basis='fp32' every stored Arnoldi
+    vector is an FP32 number and the Arnoldi relation and orthogonality hold at the FP32 level
+    (and no better: the FP64-stored basis meets the same relation at the FP64 level, far below)."""
+    n = 120
+    _, _, op, At = _system(n)
+    rng = np.random.default_rng(1)
+    C, _ = np.linalg.qr(rng.standard_normal((n, 4)))
+    C = C.astype(np.float32).astype(np.float64)
+    r = rng.standard_normal(n)
+    r = r - C @ (C.T @ r)
+    V, H, B, j, _ = G.arnoldi(op, r, C, 20, 0.0, "fp64", store="fp32")
+    assert j == 20
+    assert np.array_equal(V, V.astype(np.float32).astype(np.float64))
+    lhs = np.stack([op(V[:, i]) for i in range(j)], axis=1)
+    rel = np.linalg.norm(lhs - C @ B - V @ H) / (np.linalg.norm(At, 2) * np.sqrt(j))
+    assert rel <= 10 * (4 + j) * U32
+    W = np.hstack([C, V])
+    orth = np.abs(W.T @ W - np.eye(W.shape[1])).max()
+    assert orth <= 10 * (4 + j) * U32
+    V64, H64, B64, _, _ = G.arnoldi(op, r, C, 20, 0.0, "fp64")
+    lhs64 = np.stack([op(V64[:, i]) for i in range(j)], axis=1)
+    rel64 = np.linalg.norm(lhs64 - C @ B64 - V64 @ H64) / (np.linalg.norm(At, 2) * np.sqrt(j))
+    assert rel > 100 * rel64
+
+
+def test_fp32_basis_recycle_vectors_and_solve():
+    """With basis='fp32' the recycle vectors U, C are FP32 numbers after every solve, C^T C = I and
+    A~ U = C hold at the FP32 level, and GCRO-DR still reaches an inner tolerance of 1e-6; with
+    basis='fp64' the solve is the default one, bit for bit."""
+    n = 150
+    _, _, op, At = _system(n, kappa=1e4)
+    rng = np.random.default_rng(2)
+    Y = None
+    for step in range(3):
+        c = rng.standard_normal(n)
+        d, U, C, info = G.gcrodr(op, c, 20, 6, 1e-6, Ytil=Y, basis="fp32")
+        kk = U.shape[1]
+        assert kk > 0 and info.converged
+        for X in (U, C):
+            assert np.array_equal(X, X.astype(np.float32).astype(np.float64))
+        assert np.abs(C.T @ C - np.eye(kk)).max() <= 10 * kk * U32 * 10
+        AU = np.stack([op(U[:, i]) for i in range(kk)], axis=1)
+        assert np.linalg.norm(AU - C) / (np.linalg.norm(At, 2) * np.linalg.norm(U)) <= 1e4 * U32
+        assert np.linalg.norm(c - At @ d) <= 1.01e-6 * np.linalg.norm(c) + 1e-14
+        Y = U
+    c = rng.standard_normal(n)
+    a = G.gcrodr(op, c, 20, 6, 1e-10, basis="fp64")
+    b = G.gcrodr(op, c, 20, 6, 1e-10)
+    assert np.array_equal(a[0], b[0]) and a[3].its == b[3].its
