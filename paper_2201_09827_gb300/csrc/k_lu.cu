@@ -283,6 +283,147 @@ __device__ __forceinline__ float div_rn(float x, float p, float rp, bool p_safe)
     return __fdiv_rn(x, p);
 }
 
+// Work of a panel launch once its columns are factored (sh.top, sh.piv final): the net row moves
+// of the panel's interchanges applied to the other columns of W (FP32) and LU (u_f), and the U12
+// rows of the block's later W columns (tail.u12_mode). Every CTA of the cluster takes a share.
+template <int WC>
+__device__ __forceinline__ void panel_tail_work(PanelShared<WC>& sh, float* __restrict__ W, int64_t ldw, int64_t r0,
+                                                int wcols, const PanelTail& tail, int C, int rank, int tid,
+                                                int lane, int warp) {
+    const int64_t ncw = tail.wcol1 - tail.wcol0;
+    const int64_t ncw2 = tail.w2col1 - tail.w2col0;
+    const int64_t ncl = tail.LU ? tail.lcol1 - tail.lcol0 : 0;
+    if (ncw <= 0 && ncw2 <= 0 && ncl <= 0) return;
+    // net effect of the interchanges ipiv[r0 .. r0+wcols) as row moves (dst <- src): replay them
+    // on slot contents held in one warp's registers (slots 0..31 panel rows, 32.. the distinct
+    // pivot rows below the diagonal block, numbered by first use)
+    if (warp == 0) {
+        const unsigned FULL = 0xffffffffu;
+        const int p = (lane < wcols) ? sh.piv[lane] : lane;
+        const bool ext = lane < wcols && p >= wcols;
+        const unsigned key = ext ? (unsigned)p : (0x80000000u | (unsigned)lane);
+        const unsigned same = __match_any_sync(FULL, key);
+        const int first = __ffs(same) - 1;
+        const unsigned leaders = __ballot_sync(FULL, ext && first == lane);
+        const int nlead = __popc(leaders);
+        const int slot = ext ? 32 + __popc(leaders & ((1u << first) - 1u)) : p;
+        if (ext && first == lane) sh.ext_row[__popc(leaders & ((1u << lane) - 1u))] = p;
+        __syncwarp();
+        const int rowB = (lane < nlead) ? sh.ext_row[lane] : -1;
+        int cA = lane, cB = rowB;
+        for (int k = 0; k < wcols; ++k) {
+            const int b = __shfl_sync(FULL, slot, k);
+            const int va = __shfl_sync(FULL, cA, k);
+            const int vbA = __shfl_sync(FULL, cA, b & 31);
+            const int vbB = __shfl_sync(FULL, cB, b & 31);
+            const int vb = (b < 32) ? vbA : vbB;
+            if (lane == k) cA = vb;
+            if (b < 32) {
+                if (lane == b) cA = va;
+            } else if (lane == b - 32) {
+                cB = va;
+            }
+        }
+        const bool mA = lane < wcols && cA != lane;
+        const bool mB = lane < nlead && cB != rowB;
+        const unsigned bA = __ballot_sync(FULL, mA), bB = __ballot_sync(FULL, mB);
+        const unsigned lt = (1u << lane) - 1u;
+        if (mA) { int i = __popc(bA & lt); sh.mv_dst[i] = lane; sh.mv_src[i] = cA; }
+        if (mB) { int i = __popc(bA) + __popc(bB & lt); sh.mv_dst[i] = rowB; sh.mv_src[i] = cB; }
+        if (lane == 0) sh.mv_count = __popc(bA) + __popc(bB);
+    }
+    __syncthreads();
+    const int cnt = sh.mv_count;
+    const bool trsm = tail.u12_mode != 0;
+    if (cnt == 0 && !trsm) return;
+    // column chunks (32 FP32 columns of W, 64 u_f columns of LU) spread over the cluster's CTAs;
+    // every source of a chunk is read before any destination is written
+    const int nchw = (int)((gmax<int64_t>(ncw, 0) + 31) / 32);
+    const int nchw2 = (int)((gmax<int64_t>(ncw2, 0) + 31) / 32);
+    const int nchl = (int)((gmax<int64_t>(ncl, 0) + 63) / 64);
+    if (cnt > 0) {
+        for (int ch = rank; ch < nchw + nchw2 + nchl; ch += C) {
+            if (ch < nchw + nchw2) {
+                const bool second = ch >= nchw;
+                const int64_t cbase = second ? tail.w2col0 + (int64_t)(ch - nchw) * 32 : tail.wcol0 + (int64_t)ch * 32;
+                const int64_t cend = second ? tail.w2col1 : tail.wcol1;
+                float v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 5;
+                    const int64_t col = cbase + (e & 31);
+                    if (m < cnt && col < cend) v[k] = W[(r0 + sh.mv_src[m]) * ldw + col];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 5;
+                    const int64_t col = cbase + (e & 31);
+                    if (m < cnt && col < cend) W[(r0 + sh.mv_dst[m]) * ldw + col] = v[k];
+                }
+            } else {
+                const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw - nchw2) * 64;
+                uint16_t v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 6;
+                    const int64_t col = cbase + (e & 63);
+                    if (m < cnt && col < tail.lcol1) v[k] = tail.LU[(r0 + sh.mv_src[m]) * tail.ldl + col];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int e = tid + k * PANEL_THREADS, m = e >> 6;
+                    const int64_t col = cbase + (e & 63);
+                    if (m < cnt && col < tail.lcol1) tail.LU[(r0 + sh.mv_dst[m]) * tail.ldl + col] = v[k];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (trsm && rank < nchw) {
+        // U12 rows of this CTA's W chunks, one thread per column: forward substitution with the
+        // u_f multipliers, then rounding to u_f (stored in LU, W and UT); in mode 2 the FP32
+        // multipliers and no rounding (W only)
+        const bool rnd = tail.u12_mode == 1;
+        for (int e = tid; e < WC * WC; e += PANEL_THREADS) {
+            const int i = e / WC, q = e - (e / WC) * WC;
+            const float t = sh.top[i][q];
+            sh.l11[i][q] = (q < i) ? (rnd ? uf_to_float(float_to_uf(t, tail.fmt), tail.fmt) : t) : 0.0f;
+        }
+        __syncthreads();
+        const int myw = (nchw - rank + C - 1) / C;
+        for (int t = tid; t < myw * 32; t += PANEL_THREADS) {
+            const int64_t col = tail.wcol0 + (int64_t)(rank + (t >> 5) * C) * 32 + (t & 31);
+            if (col >= tail.wcol1) continue;
+            float x[WC];
+#pragma unroll
+            for (int i = 0; i < WC; ++i) x[i] = (i < wcols) ? W[(r0 + i) * ldw + col] : 0.0f;
+#pragma unroll
+            for (int i = 1; i < WC; ++i) {
+                float acc = x[i];
+#pragma unroll
+                for (int q = 0; q < WC; ++q)
+                    if (q < i) acc = fmaf(-sh.l11[i][q], x[q], acc);
+                x[i] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < WC; ++i) {
+                if (i < wcols) {
+                    if (rnd) {
+                        const uint16_t u = float_to_uf(x[i], tail.fmt);
+                        tail.LU[(r0 + i) * tail.ldl + col] = u;
+                        W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
+                        tail.UT[col * tail.ldut + i] = u;
+                    } else {
+                        W[(r0 + i) * ldw + col] = x[i];
+                    }
+                }
+            }
+        }
+    }
+}
+
 // GEPP of one FP32 panel (rows r0..n-1, wcols <= WC columns) by a cluster of C CTAs, each holding
 // rpc consecutive rows in shared memory. Per column: thread-owned rows give local candidates
 // (computed while the previous column's update ran) and one CTA barrier merges them. Every CTA
@@ -541,138 +682,7 @@ k_panel(float* __restrict__ W, int64_t ldw, int64_t r0, int64_t n, int wcols, in
     }
     if (local_flag) atomicOr(flags, local_flag);
 
-    const int64_t ncw = tail.wcol1 - tail.wcol0;
-    const int64_t ncw2 = tail.w2col1 - tail.w2col0;
-    const int64_t ncl = tail.LU ? tail.lcol1 - tail.lcol0 : 0;
-    if (ncw <= 0 && ncw2 <= 0 && ncl <= 0) return;
-    // net effect of the interchanges ipiv[r0 .. r0+wcols) as row moves (dst <- src): replay them
-    // on slot contents held in one warp's registers (slots 0..31 panel rows, 32.. the distinct
-    // pivot rows below the diagonal block, numbered by first use)
-    if (warp == 0) {
-        const unsigned FULL = 0xffffffffu;
-        const int p = (lane < wcols) ? sh.piv[lane] : lane;
-        const bool ext = lane < wcols && p >= wcols;
-        const unsigned key = ext ? (unsigned)p : (0x80000000u | (unsigned)lane);
-        const unsigned same = __match_any_sync(FULL, key);
-        const int first = __ffs(same) - 1;
-        const unsigned leaders = __ballot_sync(FULL, ext && first == lane);
-        const int nlead = __popc(leaders);
-        const int slot = ext ? 32 + __popc(leaders & ((1u << first) - 1u)) : p;
-        if (ext && first == lane) sh.ext_row[__popc(leaders & ((1u << lane) - 1u))] = p;
-        __syncwarp();
-        const int rowB = (lane < nlead) ? sh.ext_row[lane] : -1;
-        int cA = lane, cB = rowB;
-        for (int k = 0; k < wcols; ++k) {
-            const int b = __shfl_sync(FULL, slot, k);
-            const int va = __shfl_sync(FULL, cA, k);
-            const int vbA = __shfl_sync(FULL, cA, b & 31);
-            const int vbB = __shfl_sync(FULL, cB, b & 31);
-            const int vb = (b < 32) ? vbA : vbB;
-            if (lane == k) cA = vb;
-            if (b < 32) {
-                if (lane == b) cA = va;
-            } else if (lane == b - 32) {
-                cB = va;
-            }
-        }
-        const bool mA = lane < wcols && cA != lane;
-        const bool mB = lane < nlead && cB != rowB;
-        const unsigned bA = __ballot_sync(FULL, mA), bB = __ballot_sync(FULL, mB);
-        const unsigned lt = (1u << lane) - 1u;
-        if (mA) { int i = __popc(bA & lt); sh.mv_dst[i] = lane; sh.mv_src[i] = cA; }
-        if (mB) { int i = __popc(bA) + __popc(bB & lt); sh.mv_dst[i] = rowB; sh.mv_src[i] = cB; }
-        if (lane == 0) sh.mv_count = __popc(bA) + __popc(bB);
-    }
-    __syncthreads();
-    const int cnt = sh.mv_count;
-    const bool trsm = tail.u12_mode != 0;
-    if (cnt == 0 && !trsm) return;
-    // column chunks (32 FP32 columns of W, 64 u_f columns of LU) spread over the cluster's CTAs;
-    // every source of a chunk is read before any destination is written
-    const int nchw = (int)((gmax<int64_t>(ncw, 0) + 31) / 32);
-    const int nchw2 = (int)((gmax<int64_t>(ncw2, 0) + 31) / 32);
-    const int nchl = (int)((gmax<int64_t>(ncl, 0) + 63) / 64);
-    if (cnt > 0) {
-        for (int ch = rank; ch < nchw + nchw2 + nchl; ch += C) {
-            if (ch < nchw + nchw2) {
-                const bool second = ch >= nchw;
-                const int64_t cbase = second ? tail.w2col0 + (int64_t)(ch - nchw) * 32 : tail.wcol0 + (int64_t)ch * 32;
-                const int64_t cend = second ? tail.w2col1 : tail.wcol1;
-                float v[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int e = tid + k * PANEL_THREADS, m = e >> 5;
-                    const int64_t col = cbase + (e & 31);
-                    if (m < cnt && col < cend) v[k] = W[(r0 + sh.mv_src[m]) * ldw + col];
-                }
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int e = tid + k * PANEL_THREADS, m = e >> 5;
-                    const int64_t col = cbase + (e & 31);
-                    if (m < cnt && col < cend) W[(r0 + sh.mv_dst[m]) * ldw + col] = v[k];
-                }
-            } else {
-                const int64_t cbase = tail.lcol0 + (int64_t)(ch - nchw - nchw2) * 64;
-                uint16_t v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int e = tid + k * PANEL_THREADS, m = e >> 6;
-                    const int64_t col = cbase + (e & 63);
-                    if (m < cnt && col < tail.lcol1) v[k] = tail.LU[(r0 + sh.mv_src[m]) * tail.ldl + col];
-                }
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int e = tid + k * PANEL_THREADS, m = e >> 6;
-                    const int64_t col = cbase + (e & 63);
-                    if (m < cnt && col < tail.lcol1) tail.LU[(r0 + sh.mv_dst[m]) * tail.ldl + col] = v[k];
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (trsm && rank < nchw) {
-        // U12 rows of this CTA's W chunks, one thread per column: forward substitution with the
-        // u_f multipliers, then rounding to u_f (stored in LU, W and UT); in mode 2 the FP32
-        // multipliers and no rounding (W only)
-        const bool rnd = tail.u12_mode == 1;
-        for (int e = tid; e < WC * WC; e += PANEL_THREADS) {
-            const int i = e / WC, q = e - (e / WC) * WC;
-            const float t = sh.top[i][q];
-            sh.l11[i][q] = (q < i) ? (rnd ? uf_to_float(float_to_uf(t, tail.fmt), tail.fmt) : t) : 0.0f;
-        }
-        __syncthreads();
-        const int myw = (nchw - rank + C - 1) / C;
-        for (int t = tid; t < myw * 32; t += PANEL_THREADS) {
-            const int64_t col = tail.wcol0 + (int64_t)(rank + (t >> 5) * C) * 32 + (t & 31);
-            if (col >= tail.wcol1) continue;
-            float x[WC];
-#pragma unroll
-            for (int i = 0; i < WC; ++i) x[i] = (i < wcols) ? W[(r0 + i) * ldw + col] : 0.0f;
-#pragma unroll
-            for (int i = 1; i < WC; ++i) {
-                float acc = x[i];
-#pragma unroll
-                for (int q = 0; q < WC; ++q)
-                    if (q < i) acc = fmaf(-sh.l11[i][q], x[q], acc);
-                x[i] = acc;
-            }
-#pragma unroll
-            for (int i = 0; i < WC; ++i) {
-                if (i < wcols) {
-                    if (rnd) {
-                        const uint16_t u = float_to_uf(x[i], tail.fmt);
-                        tail.LU[(r0 + i) * tail.ldl + col] = u;
-                        W[(r0 + i) * ldw + col] = uf_to_float(u, tail.fmt);
-                        tail.UT[col * tail.ldut + i] = u;
-                    } else {
-                        W[(r0 + i) * ldw + col] = x[i];
-                    }
-                }
-            }
-        }
-    }
+    panel_tail_work<WC>(sh, W, ldw, r0, wcols, tail, C, rank, tid, lane, warp);
 }
 
 // ------------------------------------------------------------------ swaps, TRSM
