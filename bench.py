@@ -1,6 +1,9 @@
 """Benchmark: milliseconds to a normwise relative backward error <= 1e-15 for a dense n = 16384
-system with recycled mixed-precision GMRES-IR (BF16 tensor-core LU, FP64 working precision and
-residual, GCRO-DR(50, 10)), on synthetic randsvd matrices (geometric singular values, kappa_2 = 1e2).
+system with recycled mixed-precision GMRES-IR (FP16 tensor-core LU with diagonal scaling -- the
+paper's half precision --, FP64 working precision and residual, GCRO-DR(50, 10)), on synthetic
+randsvd matrices (geometric singular values, kappa_2 = 1e2). The same system with a BF16 LU, with
+k = 0 (GMRES-IR), a prolate matrix where recycling pays, and an FP64 LU solve are reported beside
+it as comparators.
 
 One step = the whole hot path on one system: gir_factor (scaling, u_f LU, diagonal-block
 inverses) + gir_solve (x0, refinement steps with FP64 residuals, GCRO-DR corrections) with
@@ -438,7 +441,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--kappa", type=float, default=1e2)
-    ap.add_argument("--uf", default="bf16")
+    ap.add_argument("--uf", default="fp16")
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--sample-n", type=int, default=3072)
@@ -587,7 +590,14 @@ def main():
                           carry_mode=1)
         ms0, (_, i0) = timed_steps(lambda: step_x(A, b, prm0), 3, 1)
         comparators["gmres_ir_same_system"] = {"ms": ms0, "its": i0.its, "total_its": i0.total_its,
-                                               "status": i0.status, "m": args.m, "k": 0}
+                                               "status": i0.status, "m": args.m, "k": 0, "uf": args.uf}
+        # the same system with a BF16 LU (not one of the paper's formats; eight bits of significand)
+        if args.uf != "bf16":
+            prm_b = gir.Params(uf="bf16", u="fp64", ur="fp64", m=args.m, k=args.k, tau=1e-8, imax=10,
+                               target_berr=1e-15, carry_mode=1)
+            msb, (_, ib) = timed_steps(lambda: step_x(A, b, prm_b), 3, 1)
+            comparators["bf16_same_system"] = {"ms": msb, "its": ib.its, "total_its": ib.total_its,
+                                               "status": ib.status, "m": args.m, "k": args.k, "uf": "bf16"}
         # recycling where the preconditioned operator has a few outlying eigenvalues: prolate
         # Toeplitz with about ten eigenvalues near zero (w = 0.5 - 5/n), (bf16, fp64, dd), m = 30
         from synth import prolate_torch
