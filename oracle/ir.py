@@ -60,6 +60,7 @@ class Params:
     carry_mode: int = 0
     lu_mode: str = "block"        # 'block' or 'chop'
     lu_w: int = 64
+    lu_order: str = "dot"         # FP32 summation order of the block LU's U12 and trailing update
     max_its: int | None = None    # Arnoldi steps per GCRO-DR call
     basis: str | None = None      # storage format of the Krylov and recycle basis vectors (None: u)
 
@@ -132,7 +133,7 @@ def forward_err(x, xstar):
 def factor(A, p: Params):
     if p.lu_mode == "chop":
         return lum.lu_chop(A, p.uf)
-    return lum.lu_block(A, p.uf, w=p.lu_w)
+    return lum.lu_block(A, p.uf, w=p.lu_w, order=p.lu_order)
 
 
 def solve(A, b, p: Params, F=None, xstar=None, transpose=False, Y0=None):

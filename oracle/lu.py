@@ -164,7 +164,7 @@ def lu_chop(A, fmt):
     return Factors(n, fmt, L, U, perm, ipiv, np.ones(n), np.ones(n), 1.0, mode="chop")
 
 
-def lu_block(A, fmt, w=64, scale=True):
+def lu_block(A, fmt, w=64, scale=True, order="dot"):
     """Block-FMA LU in precision ``fmt`` with block-column width ``w`` (the tensor-core model).
 
     Steps per block column [c0, c1):
@@ -174,8 +174,14 @@ def lu_block(A, fmt, w=64, scale=True):
       3. U12 = L11^-1 W[c0:c1, c1:] by FP32 substitution with the stored (rounded) L11, then
          rounded to ``fmt``.
       4. W[c1:, c1:] = fl32(W[c1:, c1:] - L21 U12) with the rounded operands.
+    ``order`` is the FP32 summation order of steps 3 and 4, which the paper leaves open:
+    'dot' rounds each entry once after its whole sum of products (the reference reading);
+    'fma' subtracts the products one at a time in column order, rounding to FP32 after each
+    (an FP32 fused multiply-add chain over the w columns). The products are exact in both.
     ``scale`` applies the fp16 equilibration (R, S, mu). fmt='fp64' gives plain GEPP in FP64.
     """
+    if order not in ("dot", "fma"):
+        raise ValueError(order)
     A = np.array(A, dtype=np.float64)
     n = A.shape[0]
     if scale:
@@ -220,11 +226,19 @@ def lu_block(A, fmt, w=64, scale=True):
             L11 = Lst[c0:c1, c0:c1] + np.eye(wd)
             X = W[c0:c1, c1:].copy()
             for r in range(1, wd):
-                X[r] = f32(X[r] - L11[r, :r] @ X[:r])
+                if order == "dot":
+                    X[r] = f32(X[r] - L11[r, :r] @ X[:r])
+                else:
+                    for q in range(r):
+                        X[r] = f32(X[r] - L11[r, q] * X[q])
             U12 = quantize_operand(X, fmt, c0, c1)
             Ust[c0:c1, c1:] = U12
             W[c0:c1, c1:] = X
-            W[c1:, c1:] = f32(W[c1:, c1:] - Lst[c1:, c0:c1] @ U12)
+            if order == "dot":
+                W[c1:, c1:] = f32(W[c1:, c1:] - Lst[c1:, c0:c1] @ U12)
+            else:
+                for q in range(wd):
+                    W[c1:, c1:] = f32(W[c1:, c1:] - np.outer(Lst[c1:, c0 + q], U12[q]))
             if not np.all(np.isfinite(W[c1:, c1:])):
                 raise NonFiniteError("overflow in the Schur complement")
     L = Lst + np.eye(n)

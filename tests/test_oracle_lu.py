@@ -111,13 +111,15 @@ def _round_operand_frac(X, fmt, row0, col0, tile):
     return out
 
 
-def block_lu_rational(A, fmt, w, tile=None, round_l=True, round_u12=True):
+def block_lu_rational(A, fmt, w, tile=None, round_l=True, round_u12=True, order="dot"):
     """The block-FMA LU model in exact rational arithmetic with explicit roundings, written
     from its definition independently of oracle.lu: per block column, GEPP of the panel with
     FP32 quotients and FP32 fused updates (ties to the lowest row), the panel's L and U11 rounded
     to fmt, U12 by FP32 substitution (exact dot, one rounding) with the rounded L11, then rounded
     to fmt, and the trailing matrix fl32(W - L21 U12) from the rounded operands (exact dot, one
-    rounding). round_l / round_u12 switch off one rounding, to show the comparison sees it."""
+    rounding). order='fma' rounds after every single product instead (in column order), in both
+    the substitution and the trailing update. round_l / round_u12 switch off one rounding, to
+    show the comparison sees it."""
     n = len(A)
     if fmt == "e4m3":
         w = tile
@@ -155,14 +157,22 @@ def block_lu_rational(A, fmt, w, tile=None, round_l=True, round_u12=True):
             X = [list(W[i][c1:]) for i in range(c0, c1)]
             for r in range(1, wd):
                 for j in range(n - c1):
-                    X[r][j] = f32(X[r][j] - sum(Ls[c0 + r][c0 + q] * X[q][j] for q in range(r)))
+                    if order == "dot":
+                        X[r][j] = f32(X[r][j] - sum(Ls[c0 + r][c0 + q] * X[q][j] for q in range(r)))
+                    else:
+                        for q in range(r):
+                            X[r][j] = f32(X[r][j] - Ls[c0 + r][c0 + q] * X[q][j])
             U12 = _round_operand_frac(X, fmt, c0, c1, tile) if round_u12 else X
             for i in range(wd):
                 W[c0 + i][c1:] = X[i]
                 Us[c0 + i][c1:] = U12[i]
             for i in range(c1, n):
                 for j in range(c1, n):
-                    W[i][j] = f32(W[i][j] - sum(Ls[i][c0 + q] * U12[q][j - c1] for q in range(wd)))
+                    if order == "dot":
+                        W[i][j] = f32(W[i][j] - sum(Ls[i][c0 + q] * U12[q][j - c1] for q in range(wd)))
+                    else:
+                        for q in range(wd):
+                            W[i][j] = f32(W[i][j] - Ls[i][c0 + q] * U12[q][j - c1])
     LU = [[float(Ls[i][j]) if i > j else float(Us[i][j]) for j in range(n)] for i in range(n)]
     return np.array(LU), piv
 
@@ -182,6 +192,32 @@ def test_block_multipanel_matches_rational(fmt, n, w):
     for kw in ({"round_l": False}, {"round_u12": False}):
         alt, _ = block_lu_rational(A, fmt, w, **kw)
         assert not np.array_equal(got, alt), kw
+
+
+@pytest.mark.parametrize("fmt,n,w", [("bf16", 9, 3), ("fp16", 8, 3), ("bf16", 10, 4)])
+def test_block_fma_order_matches_rational(fmt, n, w):
+    """The 'fma' summation order (one FP32 rounding per product, in column order, in U12 and in the
+    trailing update) equals its rational restatement bit for bit, and the rounding of U12 is seen."""
+    rng = np.random.default_rng(300 + 10 * n + w)
+    A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-2, 2, (n, n)))
+    F = lum.lu_block(A, fmt, w=w, scale=False, order="fma")
+    ref, piv = block_lu_rational(A, fmt, w, order="fma")
+    assert list(F.ipiv) == piv
+    assert np.array_equal(np.tril(F.L, -1) + F.U, ref)
+    alt, _ = block_lu_rational(A, fmt, w, order="fma", round_u12=False)
+    assert not np.array_equal(np.tril(F.L, -1) + F.U, alt)
+
+
+def test_block_orders_differ_and_both_factor():
+    """The two summation orders give different u_f factors on a 96 x 96 randsvd matrix (the order
+    reaches the stored factors through their rounding), and both satisfy the backward-error bound."""
+    A = randsvd(96, 1e3, seed=5)
+    Fd = lum.lu_block(A, "bf16", w=32, order="dot")
+    Ff = lum.lu_block(A, "bf16", w=32, order="fma")
+    assert not np.array_equal(Fd.U, Ff.U)
+    for F in (Fd, Ff):
+        E = A[F.perm] - F.L @ F.U
+        assert np.abs(E).max() <= 8 * UNIT_ROUNDOFF["bf16"] * (np.abs(F.L) @ np.abs(F.U)).max()
 
 
 def test_block_fp8_tiles_match_rational(monkeypatch):
