@@ -236,9 +236,18 @@ def lu_block(A, fmt, w=64, scale=True, order="dot"):
             W[c0:c1, c1:] = X
             if order == "dot":
                 W[c1:, c1:] = f32(W[c1:, c1:] - Lst[c1:, c0:c1] @ U12)
+            elif work == "fp32":
+                # products of two u_f values are exact in FP32, so each FP32 subtraction below is
+                # one correctly rounded fused multiply-add
+                Wt = W[c1:, c1:].astype(np.float32)
+                L32 = Lst[c1:, c0:c1].astype(np.float32)
+                U32 = U12.astype(np.float32)
+                for q in range(wd):
+                    Wt -= np.outer(L32[:, q], U32[q])
+                W[c1:, c1:] = Wt.astype(np.float64)
             else:
                 for q in range(wd):
-                    W[c1:, c1:] = f32(W[c1:, c1:] - np.outer(Lst[c1:, c0 + q], U12[q]))
+                    W[c1:, c1:] = W[c1:, c1:] - np.outer(Lst[c1:, c0 + q], U12[q])
             if not np.all(np.isfinite(W[c1:, c1:])):
                 raise NonFiniteError("overflow in the Schur complement")
     L = Lst + np.eye(n)
