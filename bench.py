@@ -309,8 +309,9 @@ def run_sweep(args, rank, world, local):
         return (r.abs().max() / (A.abs().sum(1).max() * x.abs().max() + b.abs().max())).item()
 
     n = args.n
+    parts = set(args.only.split(",")) if args.only else {"randsvd", "prolate", "convdiff", "batch", "oracle"}
     # ---- headline matrix: kappa_2 x u_f, RGMRES-IR(50, 10) and the GMRES-IR(50) comparator
-    for kappa in (1e2, 1e4, 1e6, 1e8):
+    for kappa in ((1e2, 1e4, 1e6, 1e8) if "randsvd" in parts else ()):
         A = randsvd_torch(n, kappa, seed=0, device=f"cuda:{local}")
         g = torch.Generator(device=dev)
         g.manual_seed(2)
@@ -350,7 +351,8 @@ def run_sweep(args, rank, world, local):
     # (numerically singular) and 0.499, and at n = 4096 and 16384 with about ten eigenvalues near zero
     # (w = 0.5 - 5 / n), where the recycle space carries the slow directions from step to step
     from synth import prolate_torch
-    for np_, w in ((4096, 0.25), (4096, 0.499), (4096, 0.5 - 5.0 / 4096), (n, 0.5 - 5.0 / n)):
+    for np_, w in (((4096, 0.25), (4096, 0.499), (4096, 0.5 - 5.0 / 4096), (n, 0.5 - 5.0 / n))
+                   if "prolate" in parts else ()):
         A = prolate_torch(np_, w, device=f"cuda:{local}")
         b = torch.from_numpy(rhs_uniform(np_, 0)).to(dev)
         for k in (10, 0):
@@ -366,62 +368,79 @@ def run_sweep(args, rank, world, local):
         del A, b
 
     # ---- conv-diff n=10000: forward solve + adjoint (gradient) through the autograd function
-    A0 = torch.from_numpy(convdiff(100, 50.0)).to(dev)
-    b0 = torch.from_numpy(rhs_uniform(10000, 4)).to(dev)
-    xt = torch.from_numpy(normal_vector(10000, 5)).to(dev)
-    prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=40, k=10, tau=1e-8, imax=10, target_berr=1e-15,
-                     carry_mode=1)
+    if "convdiff" in parts:
+        A0 = torch.from_numpy(convdiff(100, 50.0)).to(dev)
+        b0 = torch.from_numpy(rhs_uniform(10000, 4)).to(dev)
+        xt = torch.from_numpy(normal_vector(10000, 5)).to(dev)
+        prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=40, k=10, tau=1e-8, imax=10, target_berr=1e-15,
+                         carry_mode=1)
 
-    def fwd_bwd():
-        A = A0.detach().requires_grad_(True)
-        b = b0.detach().requires_grad_(True)
-        x = gir.GirSolve.apply(A, b, prm)
-        loss = ((x - xt) ** 2).sum()
-        loss.backward()
-        return x.detach(), A.grad, b.grad
+        def fwd_bwd():
+            A = A0.detach().requires_grad_(True)
+            b = b0.detach().requires_grad_(True)
+            x = gir.GirSolve.apply(A, b, prm)
+            loss = ((x - xt) ** 2).sum()
+            loss.backward()
+            return x.detach(), A.grad, b.grad
 
-    ms, ts, (x, dA, db) = timed(fwd_bwd, args.steps, args.warmup)
-    # the gradient against an FP64 LU solve on the same GPU (context for the timed numbers)
-    xs = torch.linalg.solve(A0, b0)
-    lam = torch.linalg.solve(A0.T, 2 * (xs - xt))
-    emit(sweep_line(args, world, "conv-diff 5-point upwind N=100 (n=10000), Pe=50, b~U(0,1); loss=||x-x_t||^2; "
-                                 "forward BF16-LU RGMRES-IR(40,10) + adjoint solve, dA, db",
-                    {"n": 10000, "uf": "bf16", "u": "fp64", "ur": "fp64", "m": 40, "k": 10}, ms, ts,
-                    {"berr_dd": berr_dd(A0, x, b0),
-                     "db_rel_err_vs_fp64_lu": ((db - lam).abs().max() / lam.abs().max()).item(),
-                     "dA_rel_err_vs_fp64_lu": ((dA + torch.outer(lam, xs)).abs().max()
-                                               / torch.outer(lam, xs).abs().max()).item()},
-                    metric="ms forward + backward (adjoint) solve, conv-diff n=10000"))
-    del A0, b0, xt, x, dA, db, xs, lam
-    torch.cuda.empty_cache()
+        ms, ts, (x, dA, db) = timed(fwd_bwd, args.steps, args.warmup)
+        # the gradient against an FP64 LU solve on the same GPU (context for the timed numbers)
+        xs = torch.linalg.solve(A0, b0)
+        lam = torch.linalg.solve(A0.T, 2 * (xs - xt))
+        emit(sweep_line(args, world, "conv-diff 5-point upwind N=100 (n=10000), Pe=50, b~U(0,1); loss=||x-x_t||^2; "
+                                     "forward BF16-LU RGMRES-IR(40,10) + adjoint solve, dA, db",
+                        {"n": 10000, "uf": "bf16", "u": "fp64", "ur": "fp64", "m": 40, "k": 10}, ms, ts,
+                        {"berr_dd": berr_dd(A0, x, b0),
+                         "db_rel_err_vs_fp64_lu": ((db - lam).abs().max() / lam.abs().max()).item(),
+                         "dA_rel_err_vs_fp64_lu": ((dA + torch.outer(lam, xs)).abs().max()
+                                                   / torch.outer(lam, xs).abs().max()).item()},
+                        metric="ms forward + backward (adjoint) solve, conv-diff n=10000"))
+        del A0, b0, xt, x, dA, db, xs, lam
+        torch.cuda.empty_cache()
 
-    # ---- batch: 512 randsvd systems, n ~ U{256..4096}, kappa_2 = 10^U(2,8), (bf16, fp64, fp64), (30, 8)
-    sizes, kappas = batch_specs(512, 256, 4096, 2.0, 8.0, seed=3)
-    As, bs = [], []
-    for i, (nn, kp) in enumerate(zip(sizes, kappas)):
-        A = randsvd_torch(nn, kp, seed=1000 + i, device=f"cuda:{local}")
-        gg = torch.Generator(device=dev)
-        gg.manual_seed(5000 + i)
-        As.append(A)
-        bs.append(A @ torch.randn(nn, dtype=torch.float64, device=dev, generator=gg))
-    prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0, carry_mode=1,
-                     max_its=4 * 30)
-    ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm), 1, 0)
-    conv = sum(1 for i in infos if i.status == 0)
-    emit(sweep_line(args, world, "batch of 512 randsvd systems, n~U{256..4096}, kappa_2=10^U(2,8), b=A x*; "
-                                 "u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u",
-                    {"systems": 512, "n_total": int(sum(sizes)), "uf": "bf16", "m": 30, "k": 8, "max_its": 120}, ms, ts,
-                    {"status": st, "converged": conv, "total_its": int(sum(i.total_its for i in infos)),
-                     "converged_by_kappa": {f"1e{e}-1e{e + 1}": [sum(1 for i, kp in zip(infos, kappas)
-                                                                     if 10 ** e <= kp < 10 ** (e + 1) and i.status == 0),
-                                                                 sum(1 for kp in kappas if 10 ** e <= kp < 10 ** (e + 1))]
-                                            for e in range(2, 8)}},
-                    metric="ms for the whole batch of 512 systems"))
-    del As, bs, xs_
-    torch.cuda.empty_cache()
+    # ---- batch: 512 randsvd systems, n ~ U{256..4096}, kappa_2 = 10^U(2,8), (bf16, fp64, fp64), (30, 8):
+    # the persistent kernel (one launch) and the worker-stream engine on the same systems
+    if "batch" in parts:
+        sizes, kappas = batch_specs(512, 256, 4096, 2.0, 8.0, seed=3)
+        As, bs = [], []
+        for i, (nn, kp) in enumerate(zip(sizes, kappas)):
+            A = randsvd_torch(nn, kp, seed=1000 + i, device=f"cuda:{local}")
+            gg = torch.Generator(device=dev)
+            gg.manual_seed(5000 + i)
+            As.append(A)
+            bs.append(A @ torch.randn(nn, dtype=torch.float64, device=dev, generator=gg))
+        prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0,
+                         carry_mode=1, max_its=4 * 30)
+        peaks, peak_kind = load_peaks()
+        for engine in ("auto", "streams"):
+            l0 = gir.launch_count()
+            ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm, engine=engine), 1, 0)
+            launches = gir.launch_count() - l0
+            conv = sum(1 for i in infos if i.status == 0)
+            # algorithmic bytes of the Arnoldi products: 8 n^2 per A v (the float-float halves of A)
+            av_bytes = sum(8.0 * nn * nn * (i.total_its + sum(i.carry_applies[:i.ir_steps]))
+                           for nn, i in zip(sizes, infos))
+            gbs = av_bytes / (ms * 1e-3) / 1e9
+            name = "one persistent launch" if engine == "auto" else "worker-stream engine"
+            emit(sweep_line(args, world, "batch of 512 randsvd systems, n~U{256..4096}, kappa_2=10^U(2,8), b=A x*; "
+                                         f"u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u; {name}",
+                            {"systems": 512, "n_total": int(sum(sizes)), "uf": "bf16", "m": 30, "k": 8,
+                             "max_its": 120, "engine": "persistent" if engine == "auto" else "streams"}, ms, ts,
+                            {"status": st, "converged": conv, "total_its": int(sum(i.total_its for i in infos)),
+                             "av_bytes": av_bytes, "av_gbs_over_batch": gbs,
+                             "av_frac_of_hbm": gbs / peaks["hbm_gbs"],
+                             "sum_ms_factor": float(sum(i.ms_factor for i in infos)),
+                             "sum_ms_solve": float(sum(i.ms_solve for i in infos)),
+                             "converged_by_kappa": {f"1e{e}-1e{e + 1}": [
+                                 sum(1 for i, kp in zip(infos, kappas) if 10 ** e <= kp < 10 ** (e + 1) and i.status == 0),
+                                 sum(1 for kp in kappas if 10 ** e <= kp < 10 ** (e + 1))] for e in range(2, 8)}},
+                            launches=launches, metric="ms for the whole batch of 512 systems"))
+            del xs_
+        del As, bs
+        torch.cuda.empty_cache()
 
     # ---- the oracle at two sizes (validates the n^3 projection of the headline's cpu_baseline)
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and "oracle" in parts:
         proj, t1, t2, expo, i1, i2 = oracle_projection(args.n, args.sample_n, args.kappa, args.uf)
         n1, n2 = args.sample_n // 2, args.sample_n
         pts = [(n1, t1, i1.paper_format()), (n2, t2, i2.paper_format())]
@@ -453,6 +472,8 @@ def main():
                     help="the measurement matrix instead of the headline: kappa_2 x u_f with the k = 0 comparator, "
                          "the FP64 LU comparator, prolate n=4096 recycling counts, conv-diff n=10000 forward + "
                          "backward, the 512-system batch and the oracle at two sizes; one JSON line per point")
+    ap.add_argument("--only", default="",
+                    help="with --sweep: a comma-separated subset of randsvd,prolate,convdiff,batch,oracle")
     args = ap.parse_args()
     rank, world, local = dist_env()
 

@@ -103,6 +103,9 @@ typedef struct {
  * products stay in u. The vectors are still held in FP64 arrays (the numerics of FP32 storage;
  * the halved basis traffic is not built). */
 #define GIR_FLAG_BASIS_FP32 0x20u
+/* gir_batch_solve only: run the batch on the pool of worker streams even where the persistent
+ * kernel could take it (see gir_batch_solve). */
+#define GIR_FLAG_BATCH_STREAMS 0x40u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64
@@ -153,11 +156,22 @@ gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const 
 /* Batch of independent systems A_i x_i = b_i of different sizes n[i] (host array), each
  * solved by Algorithm 4 with its own factorization and recycle space. A, b, x: host arrays of
  * device pointers (lda: host array). infos: host array of nsys entries (may be NULL).
- * The systems run concurrently, largest n first, on a pool of worker streams (one host thread
- * each); the pool size and each system's LU block width come from the autotuner's table
- * (gir_autotune; GIR_FLAG_AUTOTUNE tunes missing size classes first) or from defaults.
- * The workers start after the work already enqueued on `stream`, and `stream` waits for all
- * of them. Returns GIR_OK, else the worst status of a system. Not in the paper. */
+ * Two engines, same results up to rounding:
+ *  - the persistent kernel (default where it applies: u_f GIR_BF16 or GIR_FP16, ua GIR_FP64,
+ *    neither GIR_FLAG_CW_BERR nor GIR_FLAG_SIR, every n <= 8192, m <= 100): ONE kernel launch,
+ *    captured in a CUDA graph that is launched on `stream`, whose CTAs (one per SM) take the
+ *    systems from a device queue, largest n first, and each run all of Algorithm 4 on a system
+ *    with no host round trip (the stop tests, restart sizes and recycle ranks are decided on the
+ *    device). Its LU is the block-column model with 32-column panels (factors equal in model to
+ *    gir_factor's, not bit for bit). The per-system ms_factor / ms_solve are device-clock
+ *    intervals of the CTA that ran the system. Workspace: about 10 n_max^2 bytes per CTA, fewer
+ *    CTAs if device memory is short;
+ *  - the pool of worker streams (otherwise, or with GIR_FLAG_BATCH_STREAMS): each system through
+ *    gir_factor + gir_solve on one of the worker streams (one host thread each); the pool size
+ *    and each system's LU block width come from the autotuner's table (gir_autotune;
+ *    GIR_FLAG_AUTOTUNE tunes missing size classes first) or from defaults.
+ * Both start after the work already enqueued on `stream` and synchronise it. Returns GIR_OK,
+ * else the worst status of a system (GIR_INVALID_ARG for invalid parameters). Not in the paper. */
 gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
                            const double* const* b, double* const* x, const gir_params* params,
                            gir_info* infos, void* stream);

@@ -1,9 +1,10 @@
 // Batches of independent systems and the autotuner that picks their launch shapes.
 //
-// gir_batch_solve runs Algorithm 4 on every system of a batch. The systems are independent
-// (no exchange step), so they are scheduled longest-first (by n, the LU is O(n^3)) onto a pool
-// of worker threads, each driving its own CUDA stream: small systems that cannot fill the GPU
-// alone run side by side. The pool size and the LU outer block width of each size class come
+// gir_batch_solve runs Algorithm 4 on every system of a batch. Where the persistent kernel
+// (k_persist.cu) implements the parameters, the whole batch is one launch of it. Otherwise the
+// systems, which are independent (no exchange step), are scheduled longest-first (by n, the LU is
+// O(n^3)) onto a pool of worker threads, each driving its own CUDA stream: small systems that
+// cannot fill the GPU alone run side by side. The pool size and the LU outer block width of each size class come
 // from a process-wide table filled by gir_autotune, which times the candidates on synthetic
 // matrices of the class; classes without a measurement use the defaults (256, 8 workers).
 #include <algorithm>
@@ -20,6 +21,7 @@
 
 #include "gir_batch.cuh"
 #include "gir_internal.cuh"
+#include "gir_persist.cuh"
 
 namespace gir {
 namespace {
@@ -247,6 +249,8 @@ gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, c
         gir_status t = gir_autotune(n, nsys, caller);
         if (t != GIR_OK) return t;
     }
+    if (persistent_batch_supported(nsys, n, lda, params))
+        return persistent_batch_solve(nsys, n, A, lda, b, x, params, infos, caller);
     gir_params p = *params;
     p.flags = 0;
     // longest first: the LU is O(n^3), so this keeps the largest systems off the tail

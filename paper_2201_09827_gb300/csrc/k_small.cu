@@ -21,8 +21,8 @@ namespace gir {
 __device__ __forceinline__ double sgn(double a, double b) { return b >= 0.0 ? fabs(a) : -fabs(a); }
 
 // ------------------------------------------------------------------ Givens step
-__global__ void k_givens_step(SmallState* st) {
-    if (threadIdx.x != 0) return;
+// One thread: the Givens update of column j (also called from the persistent batch kernel).
+static __device__ void givens_step_dev(SmallState* st) {
     const int j = st->j, kc = st->kc;
     // column j of B (first kc coefficients) and H (next j+1) from both CGS passes
     for (int i = 0; i < kc; ++i) st->B[i + j * SM_KMAX] = st->s1[i] + st->s2[i];
@@ -60,38 +60,13 @@ __global__ void k_givens_step(SmallState* st) {
     st->j = j + 1;
 }
 
-gir_status launch_givens_step(SmallState* st, cudaStream_t s) {
-    count_launch(), k_givens_step<<<1, 32, 0, s>>>(st);
-    GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
-}
-
-// ------------------------------------------------------------------ scale kernel
-__global__ void k_scale_by(double* __restrict__ w, int64_t n, const double* __restrict__ factor, int invert,
-                           int round32) {
-    double f = *factor;
-    if (invert) f = (f != 0.0) ? 1.0 / f : 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = w[i] * f;
-        if (round32) v = (double)__double2float_rn(v);
-        w[i] = v;
-    }
-}
-
-gir_status launch_scale_by(double* w, int64_t n, const double* factor, int invert, int round32, cudaStream_t s) {
-    int g = (int)gmin<int64_t>((n + 255) / 256, 1024);
-    count_launch(), k_scale_by<<<g, 256, 0, s>>>(w, n, factor, invert, round32);
-    GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
-}
-
 // ------------------------------------------------------------------ warp helpers
-__device__ double wsum(double v) { return warp_sum(v); }
+static __device__ double wsum(double v) { return warp_sum(v); }
 
 // Householder QR of the rows x cols column-major matrix X (ld) in place; R in the upper
 // triangle, reflector vectors below (v[0] implicit 1), tau[] the coefficients. Positive R_ii
 // is NOT enforced here.
-__device__ void house_qr(double* X, int ld, int rows, int cols, double* tau) {
+static __device__ void house_qr(double* X, int ld, int rows, int cols, double* tau) {
     const int lane = LANE;
     for (int k = 0; k < cols && k < rows; ++k) {
         // norm of X[k:rows, k]
@@ -126,7 +101,7 @@ __device__ void house_qr(double* X, int ld, int rows, int cols, double* tau) {
 }
 
 // Apply Q^T (from house_qr of X) to the rows x q matrix Y (ld ldy), in place.
-__device__ void house_apply_qt(const double* X, int ld, int rows, int cols, const double* tau, double* Y, int ldy,
+static __device__ void house_apply_qt(const double* X, int ld, int rows, int cols, const double* tau, double* Y, int ldy,
                                int q) {
     const int lane = LANE;
     for (int k = 0; k < cols && k < rows; ++k) {
@@ -144,7 +119,7 @@ __device__ void house_apply_qt(const double* X, int ld, int rows, int cols, cons
 }
 
 // Form the first q columns of Q (rows x q, ld ldq) from house_qr reflectors.
-__device__ void house_form_q(const double* X, int ld, int rows, int cols, const double* tau, double* Q, int ldq,
+static __device__ void house_form_q(const double* X, int ld, int rows, int cols, const double* tau, double* Q, int ldq,
                              int q) {
     const int lane = LANE;
     for (int c = lane; c < q; c += 32)
@@ -166,7 +141,7 @@ __device__ void house_form_q(const double* X, int ld, int rows, int cols, const 
 
 // Reduce M (d x d, ld) to upper Hessenberg form in place; Qh (global, ld d) accumulates the
 // orthogonal similarity: M_orig = Qh Hm Qh^T. v scratch of length d.
-__device__ void hess_reduce(double* M, int ld, int d, double* Qh, double* v) {
+static __device__ void hess_reduce(double* M, int ld, int d, double* Qh, double* v) {
     const int lane = LANE;
     for (int e = lane; e < d * d; e += 32) Qh[e] = ((e % d) == (e / d)) ? 1.0 : 0.0;
     WSYNC();
@@ -239,7 +214,7 @@ template <> struct EpsOf<double> { static __device__ double v() { return 1.11022
 // and D = h^2 + b c they are m +- sqrt(D). For D >= 0 the root away from m is formed by
 // addition without cancellation and the other one from the product of the two, det = a e - b c.
 template <typename T>
-__device__ void eig2x2(T a, T b, T c, T e, T& r1, T& i1, T& r2, T& i2) {
+static __device__ void eig2x2(T a, T b, T c, T e, T& r1, T& i1, T& r2, T& i2) {
     const T m = T(0.5) * (a + e), h = T(0.5) * (a - e);
     const T D = h * h + b * c;
     if (D >= T(0)) {
@@ -260,7 +235,7 @@ __device__ void eig2x2(T a, T b, T c, T e, T& r1, T& i1, T& r2, T& i2) {
 // Reflector I - tau v v^T with v = (1, v1, v2) (v2 = 0 for a 2-element one) that maps the
 // column (x0, x1, x2) to (beta, 0, 0), beta = -sign(x0) ||x||. tau = 0 when nothing to do.
 template <typename T>
-__device__ void reflector3(T x0, T x1, T x2, T& tau, T& v1, T& v2) {
+static __device__ void reflector3(T x0, T x1, T x2, T& tau, T& v1, T& v2) {
     const T scale = fabs(x0) + fabs(x1) + fabs(x2);
     tau = v1 = v2 = T(0);
     if (scale == T(0) || (x1 == T(0) && x2 == T(0))) return;
@@ -274,7 +249,7 @@ __device__ void reflector3(T x0, T x1, T x2, T& tau, T& v1, T& v2) {
 }
 
 template <typename T>
-__device__ int hess_qr_eigs(T* H, int ld, int d, T* wr, T* wi) {
+static __device__ int hess_qr_eigs(T* H, int ld, int d, T* wr, T* wi) {
     const int lane = LANE;
     const T eps = EpsOf<T>::v();
     auto at = [&](int i, int j) -> T& { return H[i + j * ld]; };
@@ -390,7 +365,7 @@ __device__ int hess_qr_eigs(T* H, int ld, int d, T* wr, T* wi) {
 // adjacent rows. U (workspace, d*(d+1) doubles: packed complex upper triangle) and small
 // vectors in smem.
 // Result x (complex) in xr, xi, normalised to unit 2-norm.
-__device__ void inv_iter(const double* Hm, int ld, int d, double lr, double li, double hnorm, double* U,
+static __device__ void inv_iter(const double* Hm, int ld, int d, double lr, double li, double hnorm, double* U,
                          double* xr, double* xi, double* mr, double* mi, int* swp, double* cr, double* ci) {
     const int lane = LANE;
     double eps = 1e-14 * (hnorm > 0.0 ? hnorm : 1.0);
@@ -489,7 +464,7 @@ __device__ void inv_iter(const double* Hm, int ld, int d, double lr, double li, 
 // (largest == 1), with the conjugate-pair rule: a pair split at the boundary is taken whole
 // if k + 1 < mcap and k + 1 <= d, dropped otherwise. sel[] receives indices (a pair is
 // represented by its member with wi > 0). Returns the number of basis columns.
-__device__ int select_eigs(const double* wr, const double* wi, int d, int k, int largest, int mcap, int* sel,
+static __device__ int select_eigs(const double* wr, const double* wi, int d, int k, int largest, int mcap, int* sel,
                            int* nsel) {
     // insertion-sort indices by the key (stable)
     int order[SM_DMAX];
@@ -546,7 +521,7 @@ __device__ int select_eigs(const double* wr, const double* wi, int d, int k, int
 // double-shift Hessenberg QR iteration on a copy in `work` (d*d doubles of shared memory): in FP32
 // on a power-of-two scaled copy (eig64 == 0), or in FP64 (eig64 != 0); the selected eigenvalues
 // in sel[0..nsel) with the first basis column of each in colofs[]. Returns the number of columns.
-__device__ int eig_values(double* M, double* work, int eig64, int d, int k, int largest, int mcap, double* Qh,
+static __device__ int eig_values(double* M, double* work, int eig64, int d, int k, int largest, int mcap, double* Qh,
                           double* wr, double* wi, double* vec, int* sel, int* colofs, int* nsel_out, double* hn_out,
                           int* fail_out) {
     const int lane = LANE;
@@ -598,7 +573,7 @@ __host__ __device__ inline int eigvec_stride(int d) { return d * (d + 1) + 7 * d
 // each in wbuf): FP64 inverse iteration on the Hessenberg matrix M from the eigenvalue as shift,
 // then z = Qh x into the real basis P (d x cols, ld ldp): a real eigenvalue gives one column, a
 // conjugate pair the real and imaginary parts.
-__device__ void eig_vectors(const double* M, int d, const double* Qh, double* P, int ldp, const double* wr,
+static __device__ void eig_vectors(const double* M, int d, const double* Qh, double* P, int ldp, const double* wr,
                             const double* wi, const int* sel, const int* colofs, int nsel, double hn, double* wbuf,
                             int nw) {
     const int lane = LANE, warp = threadIdx.x >> 5;
@@ -635,18 +610,25 @@ __device__ void eig_vectors(const double* M, int d, const double* Qh, double* P,
 constexpr int CLOSE_THREADS = 128;
 constexpr int CLOSE_SMEM_DOUBLES = 210 * 1024 / 8;
 
-// Warps that get an inverse-iteration workspace behind the (d+1) x d block M.
-__host__ __device__ inline int eigvec_warps(int d, int mrows) {
-    const int avail = CLOSE_SMEM_DOUBLES - mrows * d;
+// Warps that get an inverse-iteration workspace behind the (d+1) x d block M in a shared
+// workspace of avail_doubles doubles.
+__host__ __device__ inline int eigvec_warps(int d, int mrows, int avail_doubles) {
+    const int avail = avail_doubles - mrows * d;
     int nw = avail / eigvec_stride(d);
     nw = nw > CLOSE_THREADS / 32 ? CLOSE_THREADS / 32 : nw;
     return nw < 1 ? 1 : nw;
 }
 
+// The four warps 0..3 of the calling CTA synchronise on named barrier 1, so a larger CTA (the
+// persistent batch kernel) can run the cycle end on its first 128 threads.
+__device__ __forceinline__ void close_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 // Warp 0 runs everything but the eigenvectors, which all warps share (one selected eigenvalue
 // each at a time: GB300's FP64 pipes are per SM sub-partition, so four warps are four times one).
-__global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, double* Qh, double* Pbuf, double* Gq) {
-    extern __shared__ double smem[];
+// smem: smem_doubles doubles of shared workspace. Called by exactly the CLOSE_THREADS threads of
+// warps 0..3.
+static __device__ void cycle_close_dev(SmallState* st, double* Qh, double* Pbuf, double* Gq, double* smem,
+                                int smem_doubles) {
     const int lane = LANE, warp = threadIdx.x >> 5;
     const int j = st->j, kc = st->kc, d = kc + j;
     const int first = st->first;
@@ -796,9 +778,10 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, d
         for (int i = lane; i < d; i += 32) { st->eig_wr[i] = wr[i]; st->eig_wi[i] = wi[i]; }
     }
     }  // warp 0
-    __syncthreads();
-    if (recycle) eig_vectors(M, d, Qh, Pbuf, d, wr, wi, sel, colofs, nsel_s, hn_s, Wk, eigvec_warps(d, d + 1));
-    __syncthreads();
+    close_bar();
+    if (recycle)
+        eig_vectors(M, d, Qh, Pbuf, d, wr, wi, sel, colofs, nsel_s, hn_s, Wk, eigvec_warps(d, d + 1, smem_doubles));
+    close_bar();
     if (warp != 0) return;
     int knew = 0;
     if (recycle) {
@@ -888,23 +871,11 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, d
     if (lane == 0) st->knew = knew;
 }
 
-gir_status launch_cycle_close(SmallState* st, double* qh_scratch, cudaStream_t s) {
-    static std::atomic<unsigned> attr_done{0};
-    const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
-    GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_cycle_close, (int)smem, attr_done));
-    double* Qh = qh_scratch;
-    double* Pbuf = qh_scratch + SM_DMAX * SM_DMAX;
-    double* Gq = Pbuf + SM_DMAX * (SM_KMAX + 2);
-    count_launch(), k_cycle_close<<<1, CLOSE_THREADS, smem, s>>>(st, Qh, Pbuf, Gq);
-    GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
-}
-
 // ------------------------------------------------------------------ Cholesky of a Gram matrix
 // G2 (k x k, ld k) = R^T R; Rinv = R^-1 accumulated: Rinv <- Rinv_prev * R^-1 when
 // accumulate != 0 (Cholesky QR twice). knew = k, or 0 if the Gram matrix is not positive definite.
-__global__ void k_chol_gram(SmallState* st, int k, int accumulate) {
-    if (threadIdx.x != 0) return;
+// One thread (also called from the persistent batch kernel).
+static __device__ void chol_gram_dev(SmallState* st, int k, int accumulate) {
     if (accumulate && st->knew == 0) return;  // the first Cholesky already failed
     double* G = st->G2;
     const int ldg = k;
@@ -952,6 +923,62 @@ __global__ void k_chol_gram(SmallState* st, int k, int accumulate) {
     st->knew = k;
 }
 
+// ------------------------------------------------------------------ standalone eigen test
+// ------------------------------------------------------------------ kernels and launchers
+// Left out when another translation unit includes this file for the device functions alone
+// (the persistent batch kernel, which is not built with separate device linking).
+#ifndef GIR_SMALL_DEVICE_ONLY
+
+__global__ void k_givens_step(SmallState* st) {
+    if (threadIdx.x == 0) givens_step_dev(st);
+}
+
+gir_status launch_givens_step(SmallState* st, cudaStream_t s) {
+    count_launch(), k_givens_step<<<1, 32, 0, s>>>(st);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+// ------------------------------------------------------------------ scale kernel
+__global__ void k_scale_by(double* __restrict__ w, int64_t n, const double* __restrict__ factor, int invert,
+                           int round32) {
+    double f = *factor;
+    if (invert) f = (f != 0.0) ? 1.0 / f : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = w[i] * f;
+        if (round32) v = (double)__double2float_rn(v);
+        w[i] = v;
+    }
+}
+
+gir_status launch_scale_by(double* w, int64_t n, const double* factor, int invert, int round32, cudaStream_t s) {
+    int g = (int)gmin<int64_t>((n + 255) / 256, 1024);
+    count_launch(), k_scale_by<<<g, 256, 0, s>>>(w, n, factor, invert, round32);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+__global__ void __launch_bounds__(CLOSE_THREADS) k_cycle_close(SmallState* st, double* Qh, double* Pbuf, double* Gq) {
+    extern __shared__ double smem[];
+    cycle_close_dev(st, Qh, Pbuf, Gq, smem, CLOSE_SMEM_DOUBLES);
+}
+
+gir_status launch_cycle_close(SmallState* st, double* qh_scratch, cudaStream_t s) {
+    static std::atomic<unsigned> attr_done{0};
+    const size_t smem = (size_t)CLOSE_SMEM_DOUBLES * 8;
+    GIR_CUDA_TRY(ensure_dyn_smem((const void*)k_cycle_close, (int)smem, attr_done));
+    double* Qh = qh_scratch;
+    double* Pbuf = qh_scratch + SM_DMAX * SM_DMAX;
+    double* Gq = Pbuf + SM_DMAX * (SM_KMAX + 2);
+    count_launch(), k_cycle_close<<<1, CLOSE_THREADS, smem, s>>>(st, Qh, Pbuf, Gq);
+    GIR_CUDA_TRY(cudaGetLastError());
+    return GIR_OK;
+}
+
+__global__ void k_chol_gram(SmallState* st, int k, int accumulate) {
+    if (threadIdx.x == 0) chol_gram_dev(st, k, accumulate);
+}
+
 gir_status launch_chol_gram(SmallState* st, int k, cudaStream_t s) {
     // accumulate flag encoded in the sign of k
     int acc = k < 0;
@@ -960,7 +987,6 @@ gir_status launch_chol_gram(SmallState* st, int k, cudaStream_t s) {
     return GIR_OK;
 }
 
-// ------------------------------------------------------------------ standalone eigen test
 __global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, int d, int k, int largest, int mcap,
                                                              int eig64, double* wr_o, double* wi_o, double* P,
                                                              int* kout, double* Qh) {
@@ -987,7 +1013,7 @@ __global__ void __launch_bounds__(CLOSE_THREADS) k_small_eig(const double* Min, 
         }
     }
     __syncthreads();
-    eig_vectors(M, d, Qh, P, d, wr, wi, sel, colofs, nsel_s, hn_s, Wk, eigvec_warps(d, d + 1));
+    eig_vectors(M, d, Qh, P, d, wr, wi, sel, colofs, nsel_s, hn_s, Wk, eigvec_warps(d, d + 1, CLOSE_SMEM_DOUBLES));
     __syncthreads();
     if (warp != 0) return;
     for (int i = lane; i < d; i += 32) { wr_o[i] = wr[i]; wi_o[i] = wi[i]; }
@@ -1005,5 +1031,7 @@ gir_status launch_small_eig(const double* M, int d, int k, int largest, int mcap
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
+
+#endif  // GIR_SMALL_DEVICE_ONLY
 
 }  // namespace gir

@@ -140,6 +140,7 @@ GIR_FLAG_SIR = 0x4       # Algorithm 1 comparator: correction by substitution, n
 GIR_FLAG_ADAPTIVE_K = 0x8  # k = its_1 - 1 from the first refinement step (Section 5)
 GIR_FLAG_EIG_FP64 = 0x10  # harmonic Ritz eigenvalues by FP64 Hessenberg QR (default FP32)
 GIR_FLAG_BASIS_FP32 = 0x20  # Krylov and recycle basis vectors rounded to FP32 when stored
+GIR_FLAG_BATCH_STREAMS = 0x40  # batch_solve on the worker-stream pool instead of the persistent kernel
 
 
 @dataclass
@@ -449,11 +450,19 @@ def tune_report() -> str:
     return buf.value.decode()
 
 
-def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False):
-    """Solve independent systems A_i x_i = b_i concurrently (longest first over worker streams).
-    autotune=True measures missing size classes first (GIR_FLAG_AUTOTUNE)."""
+def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False, engine: str = "auto"):
+    """Solve independent systems A_i x_i = b_i (gir_batch_solve).
+
+    engine="auto": one persistent kernel launch for the whole batch where it applies (u_f bf16 or
+    fp16, ua fp64, no CW_BERR / SIR flag, n <= 8192, m <= 100), else the worker-stream pool;
+    engine="streams" forces the pool (GIR_FLAG_BATCH_STREAMS). autotune=True measures missing
+    size classes of the pool first (GIR_FLAG_AUTOTUNE)."""
+    if engine not in ("auto", "streams"):
+        raise ValueError(f"engine must be 'auto' or 'streams', not {engine!r}")
     if autotune:
         params = replace(params, flags=params.flags | GIR_FLAG_AUTOTUNE)
+    if engine == "streams":
+        params = replace(params, flags=params.flags | GIR_FLAG_BATCH_STREAMS)
     lib = load()
     nsys = len(As)
     ns = (C.c_int64 * nsys)(*[A.shape[0] for A in As])
