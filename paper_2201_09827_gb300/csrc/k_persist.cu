@@ -31,6 +31,7 @@
 #undef GIR_SMALL_DEVICE_ONLY
 
 #include "gir_persist.cuh"
+#include "trace.cuh"
 
 namespace gir {
 namespace pb {
@@ -70,6 +71,7 @@ struct Slot {
     double* rr;
     SmallState* st;
     double* qh;        // cycle-end scratch: Qh | Pbuf | Gq
+    float2* Dinv;      // float-float inverses of the 32 x 32 diagonal blocks: L blocks, then U blocks
 };
 
 struct Batch {
@@ -81,7 +83,11 @@ struct Batch {
     const Slot* slots;
     gir_params p;
     int KB;            // columns reserved for C (largest recycle dimension)
+    unsigned long long* prof;  // with tracing on: per CTA, NPH phase times (ns) then NPH counts
 };
+
+// Phases timed on the device clock when tracing is on (CTA time, summed over the CTAs).
+enum { PH_FACTOR = 0, PH_SPLIT, PH_GEMV, PH_MINV, PH_CGS2, PH_CLOSE, PH_RESID, PH_TOTAL, PH_MINV_DIAG, NPH };
 
 // Per-system state shared by the CTA's threads (one copy in shared memory).
 struct Ctx {
@@ -100,10 +106,37 @@ struct Ctx {
     int fmt, scaled, r32, rbasis, eig64;
     double normA, binf;
     int rc_k, rc_valid, k_run, k_open;
+    unsigned long long* prof;
     Slot sl;
 };
 
+// Carve-up of the CTA's dynamic shared memory in the refinement phase (np = n rounded up to 8).
+struct Smem {
+    float2* ys;     // float-float y of the triangular solves (np)
+    float* vh;      // float-float split of the A v input (np each)
+    float* vl;
+    int* err;              // DEV_* flags of this CTA's current system
+    double* close;  // cycle-end workspace (overlaps all of the above)
+    int close_doubles;
+};
+
 // ------------------------------------------------------------------ block-level helpers
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Phase clock: every thread reads the start (cheap); thread 0 adds the interval after the phase's
+// closing barrier.
+__device__ __forceinline__ unsigned long long ph_start(const Ctx& cx) { return cx.prof ? gtimer() : 0ull; }
+__device__ __forceinline__ void ph_end(const Ctx& cx, int ph, unsigned long long t0) {
+    if (cx.prof && threadIdx.x == 0) {
+        cx.prof[ph] += gtimer() - t0;
+        cx.prof[NPH + ph] += 1;
+    }
+}
+
 __device__ __forceinline__ double blk_sum(double v, double* red) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -181,7 +214,7 @@ __device__ void blk_gemm_nn(const double* X, int64_t ldx, int p, const double* C
 
 // ------------------------------------------------------------------ S1: scaling and the FP32 copy
 // W = fl32(mu R A S) (R, S, mu: FP16 only), ||A||_inf in FP64; returns DEV_NONFINITE on Inf/NaN.
-__device__ int scale_load(Ctx& cx, float* W, double* red) {
+__device__ __noinline__ int scale_load(Ctx& cx, float* W, double* red) {
     const int n = cx.n, w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const double* A = cx.A;
     const int64_t lda = cx.lda, ldw = cx.ldw;
@@ -268,7 +301,7 @@ __device__ void blk_argmax(float best, float val, int idx, float* fred, float* v
 
 // Block-column LU of W (n x n FP32, row-major, ldw) into LU (u_f, ldl) and perm; returns 0,
 // DEV_SINGULAR or DEV_NONFINITE. dyn: the CTA's dynamic shared memory.
-__device__ int lu_factor(Ctx& cx, float* W, uint16_t* LU, int* perm, float* Pg, float* dyn) {
+__device__ __noinline__ int lu_factor(Ctx& cx, float* W, uint16_t* LU, int* perm, float* Pg, float* dyn) {
     const int n = cx.n, fmt = cx.fmt;
     const int64_t ldw = cx.ldw, ldl = cx.ldl;
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -447,25 +480,32 @@ __device__ int lu_factor(Ctx& cx, float* W, uint16_t* LU, int* perm, float* Pg, 
         flag = __syncthreads_or(flag);
         if (flag) return DEV_NONFINITE;
     }
+    // zero padding columns [n, ldl) of the factors: the bulk copies of the solves take whole 16-byte units
+    for (int64_t e = tid; e < (int64_t)n * (ldl - n); e += NT) {
+        const int64_t i = e / (ldl - n), j = n + e % (ldl - n);
+        LU[i * ldl + j] = 0;
+    }
     __syncthreads();
     return 0;
 }
 
 // A = A_hi + A_lo (FP32 halves, row pitch ldw) into the slot's float region
-__device__ void split_matrix(Ctx& cx) {
+__device__ __noinline__ void split_matrix(Ctx& cx) {
+    const unsigned long long t0 = ph_start(cx);
     const int n = cx.n, w = threadIdx.x >> 5, l = threadIdx.x & 31;
     float* Ah = cx.sl.F;
     float* Al = cx.sl.F + (int64_t)n * cx.ldw;
     for (int i = w; i < n; i += NW) {
         const double* a = cx.A + (int64_t)i * cx.lda;
-        for (int j = l; j < n; j += 32) {
-            const double v = a[j];
+        for (int j = l; j < (int)cx.ldw; j += 32) {
+            const double v = (j < n) ? a[j] : 0.0;   // zero padding: the bulk copies take whole 16-byte units
             const float hv = __double2float_rn(v);
             Ah[(int64_t)i * cx.ldw + j] = hv;
             Al[(int64_t)i * cx.ldw + j] = __double2float_rn(v - (double)hv);
         }
     }
     __syncthreads();
+    ph_end(cx, PH_SPLIT, t0);
 }
 
 // ------------------------------------------------------------------ S5: A~ = M^-1 A
@@ -481,6 +521,12 @@ __device__ __forceinline__ void ff_mac4(float& sh, float& sl, float ah, float al
     sl += t + e;
 }
 
+__device__ __forceinline__ void ff_fold4(float* sh, float* sl) {
+    ff_acc_add(sh[0], sl[0], sh[1], sl[1]);
+    ff_acc_add(sh[2], sl[2], sh[3], sl[3]);
+    ff_acc_add(sh[0], sl[0], sh[2], sl[2]);
+}
+
 __device__ __forceinline__ void ff_warp_sum(float& sh, float& sl) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -492,140 +538,299 @@ __device__ __forceinline__ void ff_warp_sum(float& sh, float& sl) {
     }
 }
 
-// w = A v in float-float (A_hi, A_lo rows of pitch ldw, 16-byte aligned); vh, vl: shared memory
-__device__ void gemv_ff(const Ctx& cx, const double* v, double* out, float* vh, float* vl) {
+// w = A v in float-float from A_hi, A_lo (rows of pitch ldw = n rounded up to 4, zero padded): a warp
+// takes two rows at a time, each lane keeping GV_U 16-byte loads per half and row in flight, and four
+// independent float-float accumulators per row (the TwoSum chains are latency-bound, and the CTA has
+// only four warps per scheduler to hide them).
+constexpr int GV_U = 2;
+constexpr int TR_U = 2;             // triangular solves: 16-byte loads per row in flight per lane
+__device__ __noinline__ void gemv_ff(const Ctx& cx, const double* v, double* out, const Smem& sm) {
+    const unsigned long long t0 = ph_start(cx);
     const int n = cx.n, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int j = threadIdx.x; j < n; j += NT) {
-        const double x = v[j];
+    const int ldw = (int)cx.ldw, n4 = ldw >> 2;
+    for (int j = threadIdx.x; j < ldw; j += NT) {
+        const double x = (j < n) ? v[j] : 0.0;
         const float hv = __double2float_rn(x);
-        vh[j] = hv;
-        vl[j] = __double2float_rn(x - (double)hv);
+        sm.vh[j] = hv;
+        sm.vl[j] = __double2float_rn(x - (double)hv);
     }
     __syncthreads();
-    const int n4 = n >> 2;
-    for (int i = w; i < n; i += NW) {
-        const float4* rh = reinterpret_cast<const float4*>(cx.Ah + (int64_t)i * cx.ldw);
-        const float4* rl = reinterpret_cast<const float4*>(cx.Al + (int64_t)i * cx.ldw);
-        const float4* xh = reinterpret_cast<const float4*>(vh);
-        const float4* xl = reinterpret_cast<const float4*>(vl);
-        float sh = 0.0f, sl = 0.0f;
-#pragma unroll 2
-        for (int j = l; j < n4; j += 32) {
-            const float4 a = __ldcs(rh + j), b = __ldcs(rl + j);
-            const float4 c = xh[j], d = xl[j];
-            ff_mac4(sh, sl, a.x, b.x, c.x, d.x);
-            ff_mac4(sh, sl, a.y, b.y, c.y, d.y);
-            ff_mac4(sh, sl, a.z, b.z, c.z, d.z);
-            ff_mac4(sh, sl, a.w, b.w, c.w, d.w);
+    const float4* xh = reinterpret_cast<const float4*>(sm.vh);
+    const float4* xl = reinterpret_cast<const float4*>(sm.vl);
+    for (int i0 = 2 * w; i0 < n; i0 += 2 * NW) {
+        const bool two = i0 + 1 < n;
+        const float4* ra_h = reinterpret_cast<const float4*>(cx.Ah + (int64_t)i0 * ldw);
+        const float4* ra_l = reinterpret_cast<const float4*>(cx.Al + (int64_t)i0 * ldw);
+        const float4* rb_h = ra_h + (ldw >> 2);
+        const float4* rb_l = ra_l + (ldw >> 2);
+        float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int j0 = l; j0 < n4; j0 += 32 * GV_U) {
+            float4 a1[GV_U], a2[GV_U], b1[GV_U], b2[GV_U];
+#pragma unroll
+            for (int u = 0; u < GV_U; ++u) {
+                const int j = j0 + 32 * u;
+                if (j < n4) {
+                    a1[u] = __ldcs(ra_h + j);
+                    a2[u] = __ldcs(ra_l + j);
+                    if (two) {
+                        b1[u] = __ldcs(rb_h + j);
+                        b2[u] = __ldcs(rb_l + j);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < GV_U; ++u) {
+                const int j = j0 + 32 * u;
+                if (j < n4) {
+                    const float4 c = xh[j], d = xl[j];
+                    ff_mac4(ah[0], al[0], a1[u].x, a2[u].x, c.x, d.x);
+                    ff_mac4(ah[1], al[1], a1[u].y, a2[u].y, c.y, d.y);
+                    ff_mac4(ah[2], al[2], a1[u].z, a2[u].z, c.z, d.z);
+                    ff_mac4(ah[3], al[3], a1[u].w, a2[u].w, c.w, d.w);
+                    if (two) {
+                        ff_mac4(bh[0], bl[0], b1[u].x, b2[u].x, c.x, d.x);
+                        ff_mac4(bh[1], bl[1], b1[u].y, b2[u].y, c.y, d.y);
+                        ff_mac4(bh[2], bl[2], b1[u].z, b2[u].z, c.z, d.z);
+                        ff_mac4(bh[3], bl[3], b1[u].w, b2[u].w, c.w, d.w);
+                    }
+                }
+            }
         }
-        for (int j = n4 * 4 + l; j < n; j += 32)
-            ff_mac4(sh, sl, cx.Ah[(int64_t)i * cx.ldw + j], cx.Al[(int64_t)i * cx.ldw + j], vh[j], vl[j]);
-        ff_warp_sum(sh, sl);
-        if (l == 0) out[i] = (double)sh + (double)sl;
+        ff_fold4(ah, al);
+        ff_warp_sum(ah[0], al[0]);
+        if (l == 0) out[i0] = (double)ah[0] + (double)al[0];
+        if (two) {
+            ff_fold4(bh, bl);
+            ff_warp_sum(bh[0], bl[0]);
+            if (l == 0) out[i0 + 1] = (double)bh[0] + (double)bl[0];
+        }
     }
     __syncthreads();
+    ph_end(cx, PH_GEMV, t0);
 }
 
 __device__ __forceinline__ float ufv(uint16_t v, int fmt) { return uf_to_float(v, fmt); }
 
-// sum over the 4 u_f values packed in q of L[c + t] y[c + t], accumulated into (sh, sl)
-__device__ __forceinline__ void ff_dot4(float& sh, float& sl, uint2 q, const float2* y, int fmt) {
-    const float l0 = ufv((uint16_t)(q.x & 0xffffu), fmt), l1 = ufv((uint16_t)(q.x >> 16), fmt);
-    const float l2 = ufv((uint16_t)(q.y & 0xffffu), fmt), l3 = ufv((uint16_t)(q.y >> 16), fmt);
-    const float4 ya = *reinterpret_cast<const float4*>(y);
-    const float4 yb = *reinterpret_cast<const float4*>(y + 2);
-    ff_acc_prod1(sh, sl, l0, ya.x, ya.y);
-    ff_acc_prod1(sh, sl, l1, ya.z, ya.w);
-    ff_acc_prod1(sh, sl, l2, yb.x, yb.y);
-    ff_acc_prod1(sh, sl, l3, yb.z, yb.w);
+// sum over the 8 u_f values packed in q of L[c + t] y[c + t] (y: 8 float-float values), into four
+// independent float-float accumulators (sh[t % 4], sl[t % 4]): their TwoSum chains overlap
+__device__ __forceinline__ void ff_dot8(float* sh, float* sl, uint4 q, const float2* y, int fmt) {
+    const float4 y0 = *reinterpret_cast<const float4*>(y);
+    const float4 y1 = *reinterpret_cast<const float4*>(y + 2);
+    const float4 y2 = *reinterpret_cast<const float4*>(y + 4);
+    const float4 y3 = *reinterpret_cast<const float4*>(y + 6);
+    ff_acc_prod1(sh[0], sl[0], ufv((uint16_t)(q.x & 0xffffu), fmt), y0.x, y0.y);
+    ff_acc_prod1(sh[1], sl[1], ufv((uint16_t)(q.x >> 16), fmt), y0.z, y0.w);
+    ff_acc_prod1(sh[2], sl[2], ufv((uint16_t)(q.y & 0xffffu), fmt), y1.x, y1.y);
+    ff_acc_prod1(sh[3], sl[3], ufv((uint16_t)(q.y >> 16), fmt), y1.z, y1.w);
+    ff_acc_prod1(sh[0], sl[0], ufv((uint16_t)(q.z & 0xffffu), fmt), y2.x, y2.y);
+    ff_acc_prod1(sh[1], sl[1], ufv((uint16_t)(q.z >> 16), fmt), y2.z, y2.w);
+    ff_acc_prod1(sh[2], sl[2], ufv((uint16_t)(q.w & 0xffffu), fmt), y3.x, y3.y);
+    ff_acc_prod1(sh[3], sl[3], ufv((uint16_t)(q.w >> 16), fmt), y3.z, y3.w);
 }
 
-// out = fl_u(mu S U^-1 L^-1 P R w) in float-float; ys: n float2 of shared memory (16-byte aligned)
-__device__ void apply_minv(const Ctx& cx, const double* win, double* out, float2* ys) {
-    __shared__ float2 accs[PW];
+// Float-float inverses of the diagonal blocks of L (unit lower) and U (upper) for the solves: one
+// warp per block, lane j solves D x = e_j by substitution (the block staged in shared memory);
+// rows and columns past n act as the identity. Stored row by row: element (r, q) of block I of
+// triangle t at Dinv[((t nb + I) 32 + r) 32 + q].
+__device__ __noinline__ void diag_inverses(const Ctx& cx, float* dyn) {
     const int n = cx.n, fmt = cx.fmt, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int64_t ldl = cx.ldl;
-    const uint16_t* LU = cx.LU;
     const int nb = (n + PW - 1) / PW;
-    // L y = P R w (unit lower), 32-row blocks
-    for (int I = 0; I < nb; ++I) {
-        const int r0 = I * PW, rows = min(PW, n - r0);
-        for (int rr = w; rr < rows; rr += NW) {
-            const int r = r0 + rr;
-            const uint16_t* row = LU + (int64_t)r * ldl;
-            float sh = 0.0f, sl = 0.0f;
-            for (int c = l * 4; c < r0; c += 128)
-                ff_dot4(sh, sl, *reinterpret_cast<const uint2*>(row + c), ys + c, fmt);
-            ff_warp_sum(sh, sl);
-            if (l == 0) {
-                const int p = cx.perm[r];
-                const double z = cx.scaled ? cx.R[p] * win[p] : win[p];
-                ff a = ff_from_double(z);
-                ff_acc_add(a.h, a.l, -sh, -sl);
-                accs[rr] = make_float2(a.h, a.l);
+    float* D = dyn + (size_t)w * PW * (PW + 1);
+    for (int task = w; task < 2 * nb; task += NW) {
+        const int t = task / nb, I = task % nb, r0 = I * PW, rows = min(PW, n - r0);
+        for (int i = 0; i < PW; ++i) {
+            float v = (i == l) ? 1.0f : 0.0f;
+            if (i < rows && l < rows) v = ufv(cx.LU[(int64_t)(r0 + i) * cx.ldl + r0 + l], fmt);
+            if (t == 0 && l == i) v = 1.0f;   // unit diagonal of L
+            D[i * (PW + 1) + l] = v;
+        }
+        __syncwarp();
+        float xh[PW], xl[PW];
+        if (t == 0) {
+#pragma unroll
+            for (int i = 0; i < PW; ++i) {
+                float ah = (i == l) ? 1.0f : 0.0f, al = 0.0f;
+#pragma unroll
+                for (int q = 0; q < i; ++q) ff_acc_prod1(ah, al, -D[i * (PW + 1) + q], xh[q], xl[q]);
+                const ff y = ff_norm(ah, al);
+                xh[i] = y.h;
+                xl[i] = y.l;
+            }
+        } else {
+#pragma unroll
+            for (int i = PW - 1; i >= 0; --i) {
+                float ah = (i == l) ? 1.0f : 0.0f, al = 0.0f;
+#pragma unroll
+                for (int q = i + 1; q < PW; ++q) ff_acc_prod1(ah, al, -D[i * (PW + 1) + q], xh[q], xl[q]);
+                const float ud = D[i * (PW + 1) + i];
+                const float yh = __fdiv_rn(ah, ud);
+                const float rem = fmaf(-yh, ud, ah) + al;
+                const ff y = ff_norm(yh, __fdiv_rn(rem, ud));
+                xh[i] = y.h;
+                xl[i] = y.l;
             }
         }
-        __syncthreads();
-        if (w == 0) {
-            float lrow[PW];
+        float2* out = cx.sl.Dinv + ((size_t)t * nb + I) * PW * PW;
 #pragma unroll
-            for (int q = 0; q < PW; ++q)
-                lrow[q] = (q < l && l < rows) ? ufv(LU[(int64_t)(r0 + l) * ldl + r0 + q], fmt) : 0.0f;
-            float ah = 0.0f, al = 0.0f;
-            if (l < rows) { ah = accs[l].x; al = accs[l].y; }
-#pragma unroll
-            for (int q = 0; q < PW; ++q) {
-                const float yh = __shfl_sync(0xffffffffu, ah, q), yl = __shfl_sync(0xffffffffu, al, q);
-                if (l > q) ff_acc_prod1(ah, al, -lrow[q], yh, yl);
-            }
-            const ff y = ff_norm(ah, al);
-            if (l < rows) ys[r0 + l] = make_float2(y.h, y.l);
-        }
-        __syncthreads();
+        for (int i = 0; i < PW; ++i) out[i * PW + l] = make_float2(xh[i], xl[i]);
+        __syncwarp();
     }
-    // U y2 = y (upper, non-unit), in place
-    for (int I = nb - 1; I >= 0; --I) {
-        const int r0 = I * PW, rows = min(PW, n - r0), cs = r0 + rows;
-        const int c4 = cs + ((n - cs) & ~3);
-        for (int rr = w; rr < rows; rr += NW) {
-            const int r = r0 + rr;
-            const uint16_t* row = LU + (int64_t)r * ldl;
-            float sh = 0.0f, sl = 0.0f;
-            for (int c = cs + l * 4; c < c4; c += 128)
-                ff_dot4(sh, sl, *reinterpret_cast<const uint2*>(row + c), ys + c, fmt);
-            for (int c = c4 + l; c < n; c += 32) ff_acc_prod1(sh, sl, ufv(row[c], fmt), ys[c].x, ys[c].y);
-            ff_warp_sum(sh, sl);
-            if (l == 0) {
-                float ah = ys[r].x, al = ys[r].y;
-                ff_acc_add(ah, al, -sh, -sl);
-                accs[rr] = make_float2(ah, al);
-            }
-        }
-        __syncthreads();
-        if (w == 0) {
-            float urow[PW];
+    __syncthreads();
+}
+
+// out = fl_u(mu S U^-1 L^-1 P R w) in float-float, by blocks of 32 rows (L in order, then U in
+// reverse order): the block's off-diagonal sums (warp w takes rows w and w + 16), then its diagonal
+// block through the precomputed inverse with one refinement step.
+__device__ __noinline__ void apply_minv(const Ctx& cx, const double* win, double* out, const Smem& sm) {
+    __shared__ float2 accs[PW], y1s[PW], ress[PW];
+    __shared__ float2 DinvS[PW * PW];   // the diagonal block's inverse, row-major
+    __shared__ float Dg[PW][PW + 1];    // the diagonal block (unit diagonal for L, zero outside the triangle)
+    const unsigned long long t0 = ph_start(cx);
+    const int n = cx.n, fmt = cx.fmt, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int ldl = (int)cx.ldl;
+    const uint16_t* LU = cx.LU;
+    float2* ys = sm.ys;
+    const int nb = (n + PW - 1) / PW;
+    for (int j = n + threadIdx.x; j < ldl; j += NT) ys[j] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    for (int t = 0; t < 2; ++t) {
+        for (int bk = 0; bk < nb; ++bk) {
+            const int I = (t == 0) ? bk : nb - 1 - bk;
+            const int r0 = I * PW, rows = min(PW, n - r0);
+            const bool ha = w < rows, hb = w + 16 < rows;
+            // the diagonal block's inverse, loaded while the strip streams
+            const float2* di = cx.sl.Dinv + ((size_t)t * nb + I) * PW * PW;
+            const float2 dv0 = di[threadIdx.x], dv1 = di[threadIdx.x + NT];
+            float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            // rows w and w + 16 of the strip; off-diagonal columns [0, r0) of L, [r0 + 32, ldl) of U
+            // (both multiples of 8 apart), 8 per lane at a time with TR_U 16-byte loads per row in flight
+            const uint16_t* rowa = LU + (int64_t)(r0 + w) * ldl;
+            const uint16_t* rowb = LU + (int64_t)(r0 + w + 16) * ldl;
+            const int c_lo = (t == 0) ? 0 : min(r0 + PW, ldl), c_hi = (t == 0) ? r0 : ldl;
+            if (ha) {
+                for (int c0 = c_lo + l * 8; c0 < c_hi; c0 += 256 * TR_U) {
+                    uint4 qa[TR_U], qb[TR_U];
 #pragma unroll
-            for (int q = 0; q < PW; ++q)
-                urow[q] = (q > l && q < rows && l < rows) ? ufv(LU[(int64_t)(r0 + l) * ldl + r0 + q], fmt) : 0.0f;
-            const float ud = (l < rows) ? ufv(LU[(int64_t)(r0 + l) * ldl + r0 + l], fmt) : 1.0f;
-            float ah = 0.0f, al = 0.0f;
-            if (l < rows) { ah = accs[l].x; al = accs[l].y; }
+                    for (int u = 0; u < TR_U; ++u) {
+                        const int c = c0 + 256 * u;
+                        if (c < c_hi) {
+                            qa[u] = __ldg(reinterpret_cast<const uint4*>(rowa + c));
+                            if (hb) qb[u] = __ldg(reinterpret_cast<const uint4*>(rowb + c));
+                        }
+                    }
 #pragma unroll
-            for (int q = PW - 1; q >= 0; --q) {
-                if (l == q) {
-                    // (ah + al) / ud in float-float: the remainder of a correctly rounded quotient is exact
-                    const float yh = __fdiv_rn(ah, ud);
-                    const float rem = fmaf(-yh, ud, ah) + al;
-                    al = __fdiv_rn(rem, ud);
-                    ah = yh;
+                    for (int u = 0; u < TR_U; ++u) {
+                        const int c = c0 + 256 * u;
+                        if (c < c_hi) {
+                            ff_dot8(ah, al, qa[u], ys + c, fmt);
+                            if (hb) ff_dot8(bh, bl, qb[u], ys + c, fmt);
+                        }
+                    }
                 }
-                const float yh = __shfl_sync(0xffffffffu, ah, q), yl = __shfl_sync(0xffffffffu, al, q);
-                if (l < q) ff_acc_prod1(ah, al, -urow[q], yh, yl);
             }
-            const ff y = ff_norm(ah, al);
-            if (l < rows) ys[r0 + l] = make_float2(y.h, y.l);
+            // the diagonal block, masked to its triangle; rows past n are identity rows
+            {
+                const int ra = w, rb = w + 16;
+                const bool in_a = (t == 0) ? (l < ra) : (l >= ra), in_b = (t == 0) ? (l < rb) : (l >= rb);
+                Dg[ra][l] = (ha && l < rows) ? (in_a ? ufv(rowa[r0 + l], fmt) : (l == ra ? 1.0f : 0.0f))
+                                             : (l == ra ? 1.0f : 0.0f);
+                Dg[rb][l] = (hb && l < rows) ? (in_b ? ufv(rowb[r0 + l], fmt) : (l == rb ? 1.0f : 0.0f))
+                                             : (l == rb ? 1.0f : 0.0f);
+            }
+            const unsigned long long td = ph_start(cx);
+            DinvS[threadIdx.x] = dv0;
+            DinvS[threadIdx.x + NT] = dv1;
+            if (ha) {
+                ff_fold4(ah, al);
+                ff_fold4(bh, bl);
+                ff_warp_sum(ah[0], al[0]);
+                ff_warp_sum(bh[0], bl[0]);
+                if (l == 0) {
+                    const int ra = r0 + w, rb = r0 + w + 16;
+                    ff a, bq;
+                    if (t == 0) {
+                        const int pa = cx.perm[ra];
+                        a = ff_from_double(cx.scaled ? cx.R[pa] * win[pa] : win[pa]);
+                        if (hb) {
+                            const int pb = cx.perm[rb];
+                            bq = ff_from_double(cx.scaled ? cx.R[pb] * win[pb] : win[pb]);
+                        }
+                    } else {
+                        a = ff{ys[ra].x, ys[ra].y};
+                        if (hb) bq = ff{ys[rb].x, ys[rb].y};
+                    }
+                    ff_acc_add(a.h, a.l, -ah[0], -al[0]);
+                    accs[w] = make_float2(a.h, a.l);
+                    if (hb) {
+                        ff_acc_add(bq.h, bq.l, -bh[0], -bl[0]);
+                        accs[w + 16] = make_float2(bq.h, bq.l);
+                    } else {
+                        accs[w + 16] = make_float2(0.0f, 0.0f);
+                    }
+                }
+            } else if (l == 0) {
+                accs[w] = make_float2(0.0f, 0.0f);
+                accs[w + 16] = make_float2(0.0f, 0.0f);
+            }
+            __syncthreads();
+            // diagonal block: y1 = Dinv acc, then one refinement step y = y1 + Dinv (acc - D y1), which
+            // brings the explicit inverse to the accuracy of a substitution. Warp w takes rows w and
+            // w + 16, lane q the products with column q, the warp sums (float-float).
+            {
+                const int ra = w, rb = w + 16;
+                const float2 aq = accs[l];
+                const float2 ia = DinvS[ra * PW + l], ib = DinvS[rb * PW + l];
+                float pa = ia.x * aq.x, ea = fmaf(ia.x, aq.x, -pa);
+                ea = fmaf(ia.x, aq.y, fmaf(ia.y, aq.x, ea));
+                float pb = ib.x * aq.x, eb = fmaf(ib.x, aq.x, -pb);
+                eb = fmaf(ib.x, aq.y, fmaf(ib.y, aq.x, eb));
+                ff_warp_sum(pa, ea);
+                ff_warp_sum(pb, eb);
+                const ff ya = ff_norm(pa, ea), yb = ff_norm(pb, eb);
+                if (l == 0) {
+                    y1s[ra] = make_float2(ya.h, ya.l);
+                    y1s[rb] = make_float2(yb.h, yb.l);
+                }
+                __syncthreads();
+                // residual acc - D y1: lane q forms -D[r][q] y1[q]; lane 0 adds acc[r]
+                const float2 yq = y1s[l];
+                float ha_ = 0.0f, la_ = 0.0f, hb_ = 0.0f, lb_ = 0.0f;
+                ff_acc_prod1(ha_, la_, -Dg[ra][l], yq.x, yq.y);
+                ff_acc_prod1(hb_, lb_, -Dg[rb][l], yq.x, yq.y);
+                if (l == 0) {
+                    ff_acc_add(ha_, la_, accs[ra].x, accs[ra].y);
+                    ff_acc_add(hb_, lb_, accs[rb].x, accs[rb].y);
+                }
+                ff_warp_sum(ha_, la_);
+                ff_warp_sum(hb_, lb_);
+                if (l == 0) {
+                    const ff ra_ = ff_norm(ha_, la_), rb_ = ff_norm(hb_, lb_);
+                    ress[ra] = make_float2(ra_.h, ra_.l);
+                    ress[rb] = make_float2(rb_.h, rb_.l);
+                }
+                __syncthreads();
+                const float2 rq = ress[l];
+                float qa = ia.x * rq.x, fa = fmaf(ia.x, rq.x, -qa);
+                fa = fmaf(ia.x, rq.y, fmaf(ia.y, rq.x, fa));
+                float qb = ib.x * rq.x, fb = fmaf(ib.x, rq.x, -qb);
+                fb = fmaf(ib.x, rq.y, fmaf(ib.y, rq.x, fb));
+                if (l == 0) {
+                    ff_acc_add(qa, fa, ya.h, ya.l);
+                    ff_acc_add(qb, fb, yb.h, yb.l);
+                }
+                ff_warp_sum(qa, fa);
+                ff_warp_sum(qb, fb);
+                if (l == 0) {
+                    const ff za = ff_norm(qa, fa), zb = ff_norm(qb, fb);
+                    if (ra < rows) ys[r0 + ra] = make_float2(za.h, za.l);
+                    if (rb < rows) ys[r0 + rb] = make_float2(zb.h, zb.l);
+                }
+            }
+            __syncthreads();
+            ph_end(cx, PH_MINV_DIAG, td);
         }
-        __syncthreads();
     }
     for (int i = threadIdx.x; i < n; i += NT) {
         double v = (double)ys[i].x + (double)ys[i].y;
@@ -633,11 +838,13 @@ __device__ void apply_minv(const Ctx& cx, const double* win, double* out, float2
         out[i] = rnd32(v, cx.r32);
     }
     __syncthreads();
+    ph_end(cx, PH_MINV, t0);
 }
 
 // ------------------------------------------------------------------ S4: residual in u_r
 // rr = b - A x in FP64 (dd = 0) or double-double (dd = 1), stored in u
-__device__ void residual(const Ctx& cx, int dd, double* rr) {
+__device__ __noinline__ void residual(const Ctx& cx, int dd, double* rr) {
+    const unsigned long long t0 = ph_start(cx);
     const int n = cx.n, w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int i = w; i < n; i += NW) {
         const double* row = cx.A + (int64_t)i * cx.lda;
@@ -674,17 +881,10 @@ __device__ void residual(const Ctx& cx, int dd, double* rr) {
         }
     }
     __syncthreads();
+    ph_end(cx, PH_RESID, t0);
 }
 
 // ------------------------------------------------------------------ S6-S11: GCRO-DR
-struct Smem {
-    float2* ys;   // TRSV output (n)
-    float* vh;    // float-float split of the GEMV input (n each)
-    float* vl;
-    double* close;  // cycle-end workspace (overlaps the others)
-    int close_doubles;
-};
-
 __device__ __forceinline__ double* Vcol(const Ctx& cx, const Batch& B, int j) {
     return cx.sl.basis + (int64_t)(B.KB + j) * cx.n;
 }
@@ -693,17 +893,18 @@ __device__ __forceinline__ double* Creg(const Ctx& cx, const Batch& B, int kc) {
 }
 
 __device__ void apply_atilde(const Ctx& cx, const double* v, double* out, const Smem& sm) {
-    gemv_ff(cx, v, cx.sl.vtmp, sm.vh, sm.vl);
-    apply_minv(cx, cx.sl.vtmp, out, sm.ys);
+    gemv_ff(cx, v, cx.sl.vtmp, sm);
+    apply_minv(cx, cx.sl.vtmp, out, sm);
 }
 
 // One Arnoldi step j over [C V] with CGS2 (two projection passes), the norm, the Givens update
 // and the normalisation of v_{j+1}.
-__device__ void arnoldi_step(const Ctx& cx, const Batch& B, int j, int kc, const Smem& sm, double* red) {
+__device__ __noinline__ void arnoldi_step(const Ctx& cx, const Batch& B, int j, int kc, const Smem& sm, double* red) {
     const int n = cx.n;
     SmallState* st = cx.sl.st;
     double* w = Vcol(cx, B, j + 1);
     apply_atilde(cx, Vcol(cx, B, j), w, sm);
+    const unsigned long long t0 = ph_start(cx);
     const double* basis = Creg(cx, B, kc);
     const int p = kc + j + 1;
     blk_gemm_tn(basis, n, p, w, n, 1, n, st->s1, p);
@@ -719,10 +920,11 @@ __device__ void arnoldi_step(const Ctx& cx, const Batch& B, int j, int kc, const
     const double f = (hn != 0.0) ? 1.0 / hn : 0.0;
     for (int i = threadIdx.x; i < n; i += NT) w[i] = rnd32(w[i] * f, cx.rbasis);
     __syncthreads();
+    ph_end(cx, PH_CGS2, t0);
 }
 
 // Arnoldi steps of one cycle from v_1 = r / beta until convergence or `steps`; returns the steps taken.
-__device__ int run_cycle(const Ctx& cx, const Batch& B, int kc, int first, double beta, double tol, int steps,
+__device__ __noinline__ int run_cycle(const Ctx& cx, const Batch& B, int kc, int first, double beta, double tol, int steps,
                          const Smem& sm, double* red) {
     const int n = cx.n;
     SmallState* st = cx.sl.st;
@@ -755,18 +957,20 @@ __device__ int run_cycle(const Ctx& cx, const Batch& B, int kc, int first, doubl
     return j;
 }
 
-__device__ void cycle_close(const Ctx& cx, const Smem& sm) {
+__device__ __noinline__ void cycle_close(const Ctx& cx, const Smem& sm) {
     SmallState* st = cx.sl.st;
     double* Qh = cx.sl.qh;
     double* Pbuf = Qh + SM_DMAX * SM_DMAX;
     double* Gq = Pbuf + SM_DMAX * (SM_KMAX + 2);
+    const unsigned long long t0 = ph_start(cx);
     if (threadIdx.x < CLOSE_THREADS) cycle_close_dev(st, Qh, Pbuf, Gq, sm.close, sm.close_doubles);
     __syncthreads();
+    ph_end(cx, PH_CLOSE, t0);
 }
 
 // GCRO-DR(m, k) for A~ d = c from d = 0 (Algorithm 3), with the recycle space of the previous
 // refinement step (Ctx rc_k, rc_valid; slot rU, rC). Returns a DEV_* mask (0 = no error).
-__device__ int gcrodr(Ctx& cx, const Batch& B, const Smem& sm, double* red, int* its_out, int* capp_out,
+__device__ __noinline__ int gcrodr(Ctx& cx, const Batch& B, const Smem& sm, double* red, int* its_out, int* capp_out,
                       int* cycles, int* conv_out) {
     const int n = cx.n, m = B.p.m;
     const Slot& sl = cx.sl;
@@ -905,12 +1109,6 @@ __device__ int gcrodr(Ctx& cx, const Batch& B, const Smem& sm, double* red, int*
     return 0;
 }
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ gir_status dev_status(int f) {
     if (f & DEV_TIMEOUT) return GIR_TIMEOUT;
     if (f & DEV_NONFINITE) return GIR_NONFINITE;
@@ -919,7 +1117,8 @@ __device__ gir_status dev_status(int f) {
 }
 
 // Algorithm 4 on one system, by the whole CTA.
-__device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned char* dyn, Ctx& cx, double* red) {
+__device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned char* dyn, Ctx& cx, double* red,
+                          int* s_err) {
     const Sys sy = B.sys[sidx];
     gir_info* info = B.info + sidx;
     const int n = (int)sy.n;
@@ -948,6 +1147,7 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
         cx.rc_valid = 0;
         cx.k_run = B.p.k;
         cx.k_open = (B.p.flags & GIR_FLAG_ADAPTIVE_K) != 0;
+        cx.prof = B.prof ? B.prof + (size_t)blockIdx.x * 2 * NPH : nullptr;
         cx.sl = sl;
         info->status = GIR_NOT_CONVERGED;
         for (int i = 0; i <= GIR_MAX_IR; ++i) info->cw_berr[i] = -1.0;
@@ -955,11 +1155,14 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
     }
     // a fresh small state (status, counters) for this system
     for (int i = threadIdx.x; i < (int)(sizeof(SmallState) / 4); i += NT) reinterpret_cast<int*>(sl.st)[i] = 0;
+    if (threadIdx.x == 0) *s_err = 0;
     __syncthreads();
     Smem sm;
+    const int np = (n + 7) & ~7;
     sm.ys = reinterpret_cast<float2*>(dyn);
-    sm.vh = reinterpret_cast<float*>(dyn + (size_t)8 * ((n + 3) & ~3));
-    sm.vl = sm.vh + ((n + 3) & ~3);
+    sm.vh = reinterpret_cast<float*>(dyn + (size_t)8 * np);
+    sm.vl = sm.vh + np;
+    sm.err = s_err;
     sm.close = reinterpret_cast<double*>(dyn);
     sm.close_doubles = DYN_BYTES / 8;
 
@@ -968,6 +1171,7 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
     if (!f) f = lu_factor(cx, sl.F, sl.LU, sl.perm, sl.P, reinterpret_cast<float*>(dyn));
     __syncthreads();
     const unsigned long long t1 = gtimer();
+    ph_end(cx, PH_FACTOR, t0);
     if (f) {
         if (threadIdx.x == 0) {
             info->status = dev_status(f);
@@ -977,9 +1181,10 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
         return;
     }
     split_matrix(cx);
+    diag_inverses(cx, reinterpret_cast<float*>(dyn));
     const double binf = blk_norminf(cx.b, n, red);
     // x0 = M^-1 b (Algorithm 4, initial solve), stored in u
-    apply_minv(cx, cx.b, cx.x, sm.ys);
+    apply_minv(cx, cx.b, cx.x, sm);
     const double u = (B.p.u == GIR_FP32) ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
     const double target = (B.p.target_berr < 0.0) ? 2.0 * u : B.p.target_berr;
     gir_status status = GIR_NOT_CONVERGED;
@@ -1002,7 +1207,7 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
         const double fs = (rinf != 0.0) ? 1.0 / rinf : 0.0;
         for (int q = threadIdx.x; q < n; q += NT) sl.rr[q] = rnd32(sl.rr[q] * fs, cx.r32);
         __syncthreads();
-        apply_minv(cx, sl.rr, sl.c, sm.ys);
+        apply_minv(cx, sl.rr, sl.c, sm);
         int its = 0, capp = 0, conv = 0;
         const int e = gcrodr(cx, B, sm, red, &its, &capp, &cycles, &conv);
         if (e) { status = dev_status(e); break; }
@@ -1017,6 +1222,8 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
         __syncthreads();
     }
     const unsigned long long t2 = gtimer();
+    __syncthreads();
+    if (*s_err && status != GIR_NONFINITE) status = dev_status(*s_err);
     if (threadIdx.x == 0) {
         info->status = status;
         info->ir_steps = ir_steps;
@@ -1026,6 +1233,7 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
         info->ms_factor = (float)((t1 - t0) * 1e-6);
         info->ms_solve = (float)((t2 - t1) * 1e-6);
     }
+    ph_end(cx, PH_TOTAL, t0);
     __syncthreads();
 }
 
@@ -1034,6 +1242,7 @@ __global__ void __launch_bounds__(NT, 1) k_batch_persistent(const Batch B) {
     __shared__ Ctx cx;
     __shared__ double red[NW];
     __shared__ int s_q;
+    __shared__ int s_err;
     const Slot sl = B.slots[blockIdx.x];
     for (;;) {
         if (threadIdx.x == 0) s_q = atomicAdd(B.next, 1);
@@ -1041,7 +1250,7 @@ __global__ void __launch_bounds__(NT, 1) k_batch_persistent(const Batch B) {
         const int q = s_q;
         __syncthreads();
         if (q >= B.nsys) break;
-        solve_one(B, sl, B.order[q], dyn, cx, red);
+        solve_one(B, sl, B.order[q], dyn, cx, red, &s_err);
     }
 }
 
@@ -1092,6 +1301,7 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
     const size_t oF = take(sizeof(float) * 2 * nmax * ldw);
     const size_t oLU = take(sizeof(uint16_t) * nmax * ldl);
     const size_t oP = take(sizeof(float) * PW * (nmax + 1));
+    const size_t oDinv = take(sizeof(float2) * 2 * ((nmax + PW - 1) / PW) * PW * PW);
     const size_t oPerm = take(sizeof(int) * nmax);
     const size_t oR = take(sizeof(double) * nmax), oS = take(sizeof(double) * nmax);
     const size_t oBasis = take(sizeof(double) * nmax * (KB + m + 1));
@@ -1124,6 +1334,9 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
     doff += 256;
     const size_t oSlots = doff;
     doff += align256(sizeof(Slot) * nslots);
+    const bool prof = trace_on();
+    const size_t oProf = doff;
+    if (prof) doff += align256(sizeof(unsigned long long) * 2 * NPH * nslots);
     const size_t oWork = doff;
     const size_t total = doff + slot_bytes * nslots;
     unsigned char* base = nullptr;
@@ -1139,6 +1352,7 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
         q.F = reinterpret_cast<float*>(w + oF);
         q.LU = reinterpret_cast<uint16_t*>(w + oLU);
         q.P = reinterpret_cast<float*>(w + oP);
+        q.Dinv = reinterpret_cast<float2*>(w + oDinv);
         q.perm = reinterpret_cast<int*>(w + oPerm);
         q.R = reinterpret_cast<double*>(w + oR);
         q.S = reinterpret_cast<double*>(w + oS);
@@ -1164,7 +1378,8 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
         if (cudaMemcpyAsync(base + oSys, hsys.data(), sizeof(Sys) * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(base + oOrder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(base + oSlots, hsl.data(), sizeof(Slot) * nslots, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(base + oInfo, 0, sizeof(gir_info) * nsys, s) != cudaSuccess) {
+            cudaMemsetAsync(base + oInfo, 0, sizeof(gir_info) * nsys, s) != cudaSuccess ||
+            (prof && cudaMemsetAsync(base + oProf, 0, sizeof(unsigned long long) * 2 * NPH * nslots, s) != cudaSuccess)) {
             st = GIR_CUDA_ERROR;
             break;
         }
@@ -1177,6 +1392,7 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
         Bt.slots = reinterpret_cast<const Slot*>(base + oSlots);
         Bt.p = *p;
         Bt.KB = KB;
+        Bt.prof = prof ? reinterpret_cast<unsigned long long*>(base + oProf) : nullptr;
         // the queue reset and the persistent launch, captured once into a graph and launched from it
         // on the caller's stream (captured on a private stream: the legacy stream cannot capture)
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1197,6 +1413,25 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = GIR_CUDA_ERROR;
             break;
+        }
+        if (prof) {
+            std::vector<unsigned long long> hp((size_t)2 * NPH * nslots);
+            if (cudaMemcpy(hp.data(), base + oProf, hp.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) ==
+                cudaSuccess) {
+                static const char* names[NPH] = {"batch: scale + LU", "batch: split A", "batch: A v",
+                                                 "batch: M^-1",       "batch: CGS2 + Givens", "batch: cycle end",
+                                                 "batch: residual",   "batch: whole system",
+                                                 "batch: M^-1, diagonal blocks"};
+                for (int ph = 0; ph < NPH; ++ph) {
+                    double ns = 0.0;
+                    long long cnt = 0;
+                    for (int c = 0; c < nslots; ++c) {
+                        ns += (double)hp[(size_t)c * 2 * NPH + ph];
+                        cnt += (long long)hp[(size_t)c * 2 * NPH + NPH + ph];
+                    }
+                    trace_add(names[ph], ns * 1e-6, cnt);
+                }
+            }
         }
         gir_status worst = GIR_OK;
         for (int i = 0; i < nsys; ++i) {

@@ -109,6 +109,18 @@ void trace_end(int slot, const char* name, cudaStream_t s) {
     if (g_trace.open > 0) --g_trace.open;
 }
 
+void trace_add(const char* name, double ms, long long cnt) {
+    if (!g_trace.on) return;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    for (auto& g : g_trace.agg)
+        if (std::strcmp(g.name, name) == 0) {
+            g.ms += ms;
+            g.cnt += cnt;
+            return;
+        }
+    g_trace.agg.push_back({name, ms, cnt});
+}
+
 static int env_flag(const char* name) {
     const char* e = getenv(name);
     return (e && e[0] == '1') ? 1 : 0;

