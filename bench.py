@@ -310,6 +310,7 @@ def run_sweep(args, rank, world, local):
 
     n = args.n
     parts = set(args.only.split(",")) if args.only else {"randsvd", "prolate", "convdiff", "batch", "oracle"}
+    # (batch-small, the 24-system counter-capture workload, runs only when named)
     # ---- headline matrix: kappa_2 x u_f, RGMRES-IR(50, 10) and the GMRES-IR(50) comparator
     for kappa in ((1e2, 1e4, 1e6, 1e8) if "randsvd" in parts else ()):
         A = randsvd_torch(n, kappa, seed=0, device=f"cuda:{local}")
@@ -439,6 +440,28 @@ def run_sweep(args, rank, world, local):
         del As, bs
         torch.cuda.empty_cache()
 
+    # ---- a small batch for counter captures of the persistent kernel: 24 randsvd systems,
+    # n ~ U{1024..2048}, kappa_2 = 10^U(2,3) (seed 5), one launch, one CTA per system
+    if "batch-small" in parts:
+        rng = np.random.default_rng(5)
+        sizes = [int(v) for v in rng.integers(1024, 2049, 24)]
+        As, bs = [], []
+        for i, nn in enumerate(sizes):
+            A = randsvd_torch(nn, 10 ** rng.uniform(2, 3), seed=900 + i, device=f"cuda:{local}")
+            gg = torch.Generator(device=dev)
+            gg.manual_seed(77 + i)
+            As.append(A)
+            bs.append(A @ torch.randn(nn, dtype=torch.float64, device=dev, generator=gg))
+        prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0,
+                         carry_mode=1, max_its=4 * 30)
+        ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm), max(1, args.steps), args.warmup)
+        emit(sweep_line(args, world, "small batch of 24 randsvd systems, n~U{1024..2048}, kappa_2=10^U(2,3); "
+                                     "u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u; one persistent launch",
+                        {"systems": 24, "uf": "bf16", "m": 30, "k": 8, "max_its": 120, "engine": "persistent"},
+                        ms, ts, {"status": st, "total_its": int(sum(i.total_its for i in infos))},
+                        metric="ms for the whole batch of 24 systems"))
+        del As, bs, xs_
+
     # ---- the oracle at two sizes (validates the n^3 projection of the headline's cpu_baseline)
     if rank == 0 and not args.no_cpu and "oracle" in parts:
         proj, t1, t2, expo, i1, i2 = oracle_projection(args.n, args.sample_n, args.kappa, args.uf)
@@ -473,7 +496,8 @@ def main():
                          "the FP64 LU comparator, prolate n=4096 recycling counts, conv-diff n=10000 forward + "
                          "backward, the 512-system batch and the oracle at two sizes; one JSON line per point")
     ap.add_argument("--only", default="",
-                    help="with --sweep: a comma-separated subset of randsvd,prolate,convdiff,batch,oracle")
+                    help="with --sweep: a comma-separated subset of randsvd,prolate,convdiff,batch,oracle, or "
+                         "batch-small (24 systems for counter captures of the persistent kernel)")
     args = ap.parse_args()
     rank, world, local = dist_env()
 
