@@ -52,7 +52,7 @@ struct Sys {
 
 // Workspace of one CTA, sized for the largest order of the batch (nmax).
 struct Slot {
-    float* F;          // 2 nmax ldwmax floats: the LU's FP32 work matrix W, then A_hi | A_lo
+    float* F;          // 2 nmax ldwmax floats: the LU's FP32 work matrix W, then A_hi and A_lo interleaved
     uint16_t* LU;      // nmax ldlmax u_f patterns: L strictly lower, U upper
     float* P;          // panel (column-major) when it does not fit in shared memory
     int* perm;
@@ -96,8 +96,7 @@ struct Ctx {
     const double* A;
     const double* b;
     double* x;
-    const float* Ah;
-    const float* Al;
+    const float* Af;   // A_hi and A_lo interleaved (see split_matrix)
     const uint16_t* LU;
     const int* perm;
     const double* R;
@@ -489,19 +488,21 @@ __device__ __noinline__ int lu_factor(Ctx& cx, float* W, uint16_t* LU, int* perm
     return 0;
 }
 
-// A = A_hi + A_lo (FP32 halves, row pitch ldw) into the slot's float region
+// A = A_hi + A_lo (FP32 halves) into the slot's float region, row i at 2 i ldw, the halves interleaved
+// by groups of four columns
 __device__ __noinline__ void split_matrix(Ctx& cx) {
     const unsigned long long t0 = ph_start(cx);
     const int n = cx.n, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    float* Ah = cx.sl.F;
-    float* Al = cx.sl.F + (int64_t)n * cx.ldw;
+    float* F = cx.sl.F;
     for (int i = w; i < n; i += NW) {
         const double* a = cx.A + (int64_t)i * cx.lda;
+        float* row = F + (int64_t)i * 2 * cx.ldw;
         for (int j = l; j < (int)cx.ldw; j += 32) {
-            const double v = (j < n) ? a[j] : 0.0;   // zero padding: the bulk copies take whole 16-byte units
+            const double v = (j < n) ? a[j] : 0.0;   // zero padding to whole groups of 4
             const float hv = __double2float_rn(v);
-            Ah[(int64_t)i * cx.ldw + j] = hv;
-            Al[(int64_t)i * cx.ldw + j] = __double2float_rn(v - (double)hv);
+            const int g = j >> 2, k = j & 3;
+            row[8 * g + k] = hv;                                   // A_hi of columns 4g .. 4g+3
+            row[8 * g + 4 + k] = __double2float_rn(v - (double)hv);  // then their A_lo
         }
     }
     __syncthreads();
@@ -538,7 +539,8 @@ __device__ __forceinline__ void ff_warp_sum(float& sh, float& sl) {
     }
 }
 
-// w = A v in float-float from A_hi, A_lo (rows of pitch ldw = n rounded up to 4, zero padded): a warp
+// w = A v in float-float from A_hi, A_lo (interleaved by groups of four columns, rows of 2 ldw floats with
+// ldw = n rounded up to 4, zero padded; one stream per row instead of two): a warp
 // takes two rows at a time, each lane keeping GV_U 16-byte loads per half and row in flight, and four
 // independent float-float accumulators per row (the TwoSum chains are latency-bound, and the CTA has
 // only four warps per scheduler to hide them).
@@ -559,10 +561,11 @@ __device__ __noinline__ void gemv_ff(const Ctx& cx, const double* v, double* out
     const float4* xl = reinterpret_cast<const float4*>(sm.vl);
     for (int i0 = 2 * w; i0 < n; i0 += 2 * NW) {
         const bool two = i0 + 1 < n;
-        const float4* ra_h = reinterpret_cast<const float4*>(cx.Ah + (int64_t)i0 * ldw);
-        const float4* ra_l = reinterpret_cast<const float4*>(cx.Al + (int64_t)i0 * ldw);
-        const float4* rb_h = ra_h + (ldw >> 2);
-        const float4* rb_l = ra_l + (ldw >> 2);
+        // rows interleave A_hi and A_lo by groups of four columns: float4 2j is hi, 2j+1 is lo
+        const float4* ra_h = reinterpret_cast<const float4*>(cx.Af + (int64_t)i0 * 2 * ldw);
+        const float4* ra_l = ra_h + 1;
+        const float4* rb_h = ra_h + 2 * (ldw >> 2);
+        const float4* rb_l = rb_h + 1;
         float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         float bh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int j0 = l; j0 < n4; j0 += 32 * GV_U) {
@@ -571,11 +574,11 @@ __device__ __noinline__ void gemv_ff(const Ctx& cx, const double* v, double* out
             for (int u = 0; u < GV_U; ++u) {
                 const int j = j0 + 32 * u;
                 if (j < n4) {
-                    a1[u] = __ldcs(ra_h + j);
-                    a2[u] = __ldcs(ra_l + j);
+                    a1[u] = __ldcs(ra_h + 2 * j);
+                    a2[u] = __ldcs(ra_l + 2 * j);
                     if (two) {
-                        b1[u] = __ldcs(rb_h + j);
-                        b2[u] = __ldcs(rb_l + j);
+                        b1[u] = __ldcs(rb_h + 2 * j);
+                        b2[u] = __ldcs(rb_l + 2 * j);
                     }
                 }
             }
@@ -1131,8 +1134,7 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
         cx.A = sy.A;
         cx.b = sy.b;
         cx.x = sy.x;
-        cx.Ah = sl.F;
-        cx.Al = sl.F + (int64_t)n * cx.ldw;
+        cx.Af = sl.F;
         cx.LU = sl.LU;
         cx.perm = sl.perm;
         cx.R = sl.R;
