@@ -176,6 +176,12 @@ gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, c
                            const double* const* b, double* const* x, const gir_params* params,
                            gir_info* infos, void* stream);
 
+/* Which engine gir_batch_solve would use for these sizes (n, lda: host arrays of nsys entries) and
+ * parameters: 1 = the persistent kernel, 0 = the worker-stream engine, -1 = nsys < 1 or a NULL
+ * pointer. Host logic only (no device call, no allocation); does not validate the parameters
+ * otherwise (gir_batch_solve reports GIR_INVALID_ARG). Not in the paper. */
+int gir_batch_engine(int nsys, const int64_t* n, const int64_t* lda, const gir_params* params);
+
 /* Autotuner (not in the paper). For each size class (n in (2^(c-1), 2^c]) of the count sizes in
  * n (host array), times gir_factor on a synthetic matrix of the class's largest order with LU
  * outer block widths 64, 128 and 256, and times a synthetic batch of factorizations of the

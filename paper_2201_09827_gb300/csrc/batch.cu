@@ -239,6 +239,11 @@ int gir_tune_report(char* buf, int buflen) {
     return (int)out.size() + 1;
 }
 
+int gir_batch_engine(int nsys, const int64_t* n, const int64_t* lda, const gir_params* params) {
+    if (nsys < 1 || !n || !lda || !params) return -1;
+    return gir::persistent_batch_supported(nsys, n, lda, params) ? 1 : 0;
+}
+
 gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
                            const double* const* b, double* const* x, const gir_params* params, gir_info* infos,
                            void* stream) {

@@ -48,6 +48,7 @@ SYMBOLS = {
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(CParams), C.POINTER(CInfo),
                                   C.c_void_p]),
     "gir_autotune": (C.c_int, [C.POINTER(C.c_int64), C.c_int, C.c_void_p]),
+    "gir_batch_engine": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(CParams)]),
     "gir_tune_report": (C.c_int, [C.c_char_p, C.c_int]),
     "gir_adjoint_grad_a": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
     "gir_free": (None, [C.c_void_p]),
@@ -448,6 +449,19 @@ def tune_report() -> str:
     buf = C.create_string_buffer(need)
     lib.gir_tune_report(buf, need)
     return buf.value.decode()
+
+
+def batch_engine(sizes, params: Params, ldas=None) -> str:
+    """'persistent' or 'streams': the engine gir_batch_solve picks for these orders and parameters."""
+    sizes = [int(v) for v in sizes]
+    ldas = [int(v) for v in (ldas or sizes)]
+    ns = (C.c_int64 * len(sizes))(*sizes)
+    ls = (C.c_int64 * len(ldas))(*ldas)
+    cp = params.c()
+    r = load().gir_batch_engine(len(sizes), ns, ls, C.byref(cp))
+    if r < 0:
+        raise GirError(GIR_INVALID_ARG, "gir_batch_engine")
+    return "persistent" if r == 1 else "streams"
 
 
 def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False, engine: str = "auto"):
