@@ -50,11 +50,11 @@ def _batch(count, lo, hi, klo, khi, seed, edge=()):
 
 
 def _oracle(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, target=None, carry=1, k_mode="fixed",
-            max_its=None, order="fma"):
+            max_its=None, order="fma", basis=None):
     """The oracle's settings for the persistent kernel: 32-column panels and, by default, the
     'fma' summation order of the block LU, which is the order the kernel's FP32 updates use."""
     return OP(uf=uf, u=u, ur=ur, ua="u2" if u != "fp64" else "u", m=m, k=k, tau=tau, imax=10, target=target,
-              lu_w=32, lu_order=order, max_its=max_its or 20 * m, carry_mode=carry, k_mode=k_mode)
+              lu_w=32, lu_order=order, max_its=max_its or 20 * m, carry_mode=carry, k_mode=k_mode, basis=basis)
 
 
 def test_persistent_batch_parity_with_oracle(pkg):
@@ -159,6 +159,24 @@ def test_persistent_carry_literal_and_adaptive_k(pkg):
         prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0, **gkw)
         xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
         op = _oracle(**okw)
+        for A, b, x, info in zip(As, bs, xs, infos):
+            xo, io, _, _ = osolve(A, b, op)
+            assert_parity_steps(A, b, x.cpu().numpy(), info, xo, io)
+
+
+def test_persistent_eig_fp64_and_fp32_basis(pkg):
+    """The two GCRO-DR options the kernel runs through the same device functions as the single-system
+    path: FP64 Hessenberg QR for the harmonic Ritz eigenvalues (GIR_FLAG_EIG_FP64) and FP32 storage
+    of the Krylov and recycle vectors (GIR_FLAG_BASIS_FP32, the oracle's basis='fp32'), 8 systems
+    each against the oracle, target 1e-15."""
+    sizes, _, As, bs = _batch(8, 200, 900, 2.0, 3.0, seed=19)
+    from paper_2201_09827_gb300 import gir
+    for flag, basis in ((gir.GIR_FLAG_EIG_FP64, None), (gir.GIR_FLAG_BASIS_FP32, "fp32")):
+        prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=1e-15,
+                         flags=flag)
+        assert pkg.batch_engine(sizes, prm) == "persistent"
+        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+        op = _oracle(target=1e-15, basis=basis)
         for A, b, x, info in zip(As, bs, xs, infos):
             xo, io, _, _ = osolve(A, b, op)
             assert_parity_steps(A, b, x.cpu().numpy(), info, xo, io)
