@@ -28,8 +28,22 @@ __global__ void __launch_bounds__(256) k_row_scale(const double* __restrict__ A,
     for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < n; i += warps_total) {
         double m = 0.0;
         bool bad = false;
-        for (int64_t j = lane; j < n; j += 32) {
-            double v = fabs(A[i * lda + j]);
+        const double* a = A + i * lda;
+        int64_t j0 = 0;
+        if (((lda & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0)) {
+            // 16-byte loads, four per lane in flight (the maximum does not depend on the order)
+            const int64_t n2 = n >> 1;
+#pragma unroll 4
+            for (int64_t j = lane; j < n2; j += 32) {
+                const double2 v = __ldcs(reinterpret_cast<const double2*>(a) + j);
+                const double x = fabs(v.x), y = fabs(v.y);
+                bad |= !(x <= 1.7976931348623157e308) || !(y <= 1.7976931348623157e308);
+                m = fmax(m, fmax(x, y));
+            }
+            j0 = 2 * n2;
+        }
+        for (int64_t j = j0 + lane; j < n; j += 32) {
+            double v = fabs(a[j]);
             bad |= !(v <= 1.7976931348623157e308);
             m = fmax(m, v);
         }
@@ -52,6 +66,7 @@ __global__ void __launch_bounds__(256) k_col_absmax(const double* __restrict__ A
     const int64_t i1 = min(n, i0 + 256);
     if (j >= n) return;
     double m = 0.0;
+#pragma unroll 8
     for (int64_t i = i0; i < i1; ++i) m = fmax(m, fabs(A[i * lda + j] * R[i]));
     atomicMax(colmax + j, (unsigned long long)__double_as_longlong(m));
 }
@@ -74,6 +89,7 @@ __global__ void __launch_bounds__(256) k_quantize(const double* __restrict__ A, 
     bool bad = false;
     const bool vec = ((lda & 1) == 0) && ((ldw & 1) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(W) & 7) == 0);
+    const bool vec4 = vec && ((ldw & 3) == 0) && ((reinterpret_cast<uintptr_t>(W) & 15) == 0);
     auto cvt = [&](double v, int64_t i, int64_t j) {
         if (R) v *= R[i] * S[j] * mu;
         const float f = __double2float_rn(v);
@@ -83,7 +99,19 @@ __global__ void __launch_bounds__(256) k_quantize(const double* __restrict__ A, 
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
         const double* a = A + i * lda;
         float* w = W + i * ldw;
-        if (vec) {
+        if (vec4) {
+            // four columns per thread: two 16-byte loads, one 16-byte store, two groups in flight
+            const int64_t n4 = n >> 2;
+#pragma unroll 2
+            for (int64_t q = threadIdx.x; q < n4; q += blockDim.x) {
+                const int64_t j = 4 * q;
+                const double2 v0 = __ldcs(reinterpret_cast<const double2*>(a + j));
+                const double2 v1 = __ldcs(reinterpret_cast<const double2*>(a + j + 2));
+                *reinterpret_cast<float4*>(w + j) =
+                    make_float4(cvt(v0.x, i, j), cvt(v0.y, i, j + 1), cvt(v1.x, i, j + 2), cvt(v1.y, i, j + 3));
+            }
+            for (int64_t j = 4 * n4 + threadIdx.x; j < n; j += blockDim.x) w[j] = cvt(a[j], i, j);
+        } else if (vec) {
             for (int64_t j = 2 * (int64_t)threadIdx.x; j + 1 < n; j += 2 * (int64_t)blockDim.x) {
                 const double2 v = *reinterpret_cast<const double2*>(a + j);
                 *reinterpret_cast<float2*>(w + j) = make_float2(cvt(v.x, i, j), cvt(v.y, i, j + 1));
