@@ -422,11 +422,11 @@ def run_sweep(args, rank, world, local):
             av_bytes = sum(8.0 * nn * nn * (i.total_its + sum(i.carry_applies[:i.ir_steps]))
                            for nn, i in zip(sizes, infos))
             gbs = av_bytes / (ms * 1e-3) / 1e9
-            name = "one persistent launch" if engine == "auto" else "worker-stream engine"
+            name = ("routed by the cost model: " + gir.batch_engine(sizes, prm)) if engine == "auto" else "worker-stream engine"
             emit(sweep_line(args, world, "batch of 512 randsvd systems, n~U{256..4096}, kappa_2=10^U(2,8), b=A x*; "
                                          f"u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u; {name}",
                             {"systems": 512, "n_total": int(sum(sizes)), "uf": "bf16", "m": 30, "k": 8,
-                             "max_its": 120, "engine": "persistent" if engine == "auto" else "streams"}, ms, ts,
+                             "max_its": 120, "engine": gir.batch_engine(sizes, prm) if engine == "auto" else "streams"}, ms, ts,
                             {"status": st, "converged": conv, "total_its": int(sum(i.total_its for i in infos)),
                              "av_bytes": av_bytes, "av_gbs_over_batch": gbs,
                              "av_frac_of_hbm": gbs / peaks["hbm_gbs"],
@@ -454,7 +454,8 @@ def run_sweep(args, rank, world, local):
             bs.append(A @ torch.randn(nn, dtype=torch.float64, device=dev, generator=gg))
         prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0,
                          carry_mode=1, max_its=4 * 30)
-        ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm), max(1, args.steps), args.warmup)
+        ms, ts, (xs_, infos, st) = timed(lambda: gir.batch_solve(As, bs, prm, engine="persistent"),
+                                         max(1, args.steps), args.warmup)
         emit(sweep_line(args, world, "small batch of 24 randsvd systems, n~U{1024..2048}, kappa_2=10^U(2,3); "
                                      "u_f=bf16, u=u_r=fp64, RGMRES-IR(30,8), target 2u; one persistent launch",
                         {"systems": 24, "uf": "bf16", "m": 30, "k": 8, "max_its": 120, "engine": "persistent"},

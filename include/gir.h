@@ -106,6 +106,9 @@ typedef struct {
 /* gir_batch_solve only: run the batch on the pool of worker streams even where the persistent
  * kernel could take it (see gir_batch_solve). */
 #define GIR_FLAG_BATCH_STREAMS 0x40u
+/* gir_batch_solve only: run the batch as the persistent kernel whenever the kernel implements the
+ * parameters and sizes (GIR_UNSUPPORTED otherwise), whatever the cost model below prefers. */
+#define GIR_FLAG_BATCH_PERSISTENT 0x80u
 
 #define GIR_MAX_M 112
 #define GIR_MAX_K 64
@@ -157,8 +160,9 @@ gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const 
  * solved by Algorithm 4 with its own factorization and recycle space. A, b, x: host arrays of
  * device pointers (lda: host array). infos: host array of nsys entries (may be NULL).
  * Two engines, same results up to rounding:
- *  - the persistent kernel (default where it applies: u_f GIR_BF16 or GIR_FP16, ua GIR_FP64,
- *    neither GIR_FLAG_CW_BERR nor GIR_FLAG_SIR, every n <= 8192, m <= 100): ONE kernel launch,
+ *  - the persistent kernel (where it applies: u_f GIR_BF16 or GIR_FP16, ua GIR_FP64, neither
+ *    GIR_FLAG_CW_BERR nor GIR_FLAG_SIR, every n <= 8192, m <= 100; chosen when a cost model of the
+ *    two engines on GB300 prefers it, or forced by GIR_FLAG_BATCH_PERSISTENT): ONE kernel launch,
  *    captured in a CUDA graph that is launched on `stream`, whose CTAs (one per SM) take the
  *    systems from a device queue, largest n first, and each run all of Algorithm 4 on a system
  *    with no host round trip (the stop tests, restart sizes and recycle ranks are decided on the
@@ -166,6 +170,12 @@ gir_status gir_solve_adjoint(gir_handle* h, const double* A, int64_t lda, const 
  *    gir_factor's, not bit for bit). The per-system ms_factor / ms_solve are device-clock
  *    intervals of the CTA that ran the system. Workspace: about 10 n_max^2 bytes per CTA, fewer
  *    CTAs if device memory is short;
+ *    A CTA factors and solves its system alone, so a batch of few large systems is faster on the
+ *    worker streams, where each system has the whole GPU. The cost model (gir_batch_engine)
+ *    compares the kernel's makespan, max(T1(n_max), sum T1(n_i) / CTAs) with the one-CTA time
+ *    T1(n) = 8.7e-9 n^3 + 1.8e-5 n^2 ms, against sum (2.1 + 4.0e-7 n_i^2) ms for the streams (both
+ *    measured on GB300 for well-conditioned systems; iteration-heavy batches favour the kernel
+ *    further);
  *  - the pool of worker streams (otherwise, or with GIR_FLAG_BATCH_STREAMS): each system through
  *    gir_factor + gir_solve on one of the worker streams (one host thread each); the pool size
  *    and each system's LU block width come from the autotuner's table (gir_autotune;
@@ -177,9 +187,10 @@ gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, c
                            gir_info* infos, void* stream);
 
 /* Which engine gir_batch_solve would use for these sizes (n, lda: host arrays of nsys entries) and
- * parameters: 1 = the persistent kernel, 0 = the worker-stream engine, -1 = nsys < 1 or a NULL
- * pointer. Host logic only (no device call, no allocation); does not validate the parameters
- * otherwise (gir_batch_solve reports GIR_INVALID_ARG). Not in the paper. */
+ * parameters: 1 = the persistent kernel, 0 = the worker-stream engine, -1 = nsys < 1, a NULL
+ * pointer, or GIR_FLAG_BATCH_PERSISTENT for a batch the kernel cannot take. Host logic only (reads
+ * the current device's SM count, 152 if there is no device; no allocation); does not validate the
+ * parameters otherwise (gir_batch_solve reports GIR_INVALID_ARG). Not in the paper. */
 int gir_batch_engine(int nsys, const int64_t* n, const int64_t* lda, const gir_params* params);
 
 /* Autotuner (not in the paper). For each size class (n in (2^(c-1), 2^c]) of the count sizes in

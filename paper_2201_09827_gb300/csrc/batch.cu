@@ -241,7 +241,9 @@ int gir_tune_report(char* buf, int buflen) {
 
 int gir_batch_engine(int nsys, const int64_t* n, const int64_t* lda, const gir_params* params) {
     if (nsys < 1 || !n || !lda || !params) return -1;
-    return gir::persistent_batch_supported(nsys, n, lda, params) ? 1 : 0;
+    const bool ok = gir::persistent_batch_supported(nsys, n, lda, params);
+    if (params->flags & GIR_FLAG_BATCH_PERSISTENT) return ok ? 1 : -1;
+    return (ok && gir::persistent_batch_preferred(nsys, n)) ? 1 : 0;
 }
 
 gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
@@ -254,8 +256,9 @@ gir_status gir_batch_solve(int nsys, const int64_t* n, const double* const* A, c
         gir_status t = gir_autotune(n, nsys, caller);
         if (t != GIR_OK) return t;
     }
-    if (persistent_batch_supported(nsys, n, lda, params))
-        return persistent_batch_solve(nsys, n, A, lda, b, x, params, infos, caller);
+    const int engine = gir_batch_engine(nsys, n, lda, params);
+    if (engine < 0) return GIR_UNSUPPORTED;   // the persistent kernel was asked for and cannot take it
+    if (engine == 1) return persistent_batch_solve(nsys, n, A, lda, b, x, params, infos, caller);
     gir_params p = *params;
     p.flags = 0;
     // longest first: the LU is O(n^3), so this keeps the largest systems off the tail

@@ -180,7 +180,7 @@ gir_status validate(int64_t n, int64_t lda, const gir_params* p) {
     if (p->imax < 0 || p->imax >= GIR_MAX_IR) return GIR_INVALID_ARG;
     if (!(p->tau >= 0.0)) return GIR_INVALID_ARG;
     if ((p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_CW_BERR | GIR_FLAG_SIR | GIR_FLAG_ADAPTIVE_K | GIR_FLAG_EIG_FP64 |
-                      GIR_FLAG_BASIS_FP32 | GIR_FLAG_BATCH_STREAMS)) != 0)
+                      GIR_FLAG_BASIS_FP32 | GIR_FLAG_BATCH_STREAMS | GIR_FLAG_BATCH_PERSISTENT)) != 0)
         return GIR_INVALID_ARG;
     if (p->uf != GIR_BF16 && p->uf != GIR_FP16 && p->uf != GIR_FP8_E4M3) return GIR_UNSUPPORTED;
     if (p->u != GIR_FP64 && p->u != GIR_FP32) return GIR_UNSUPPORTED;

@@ -14,6 +14,10 @@ constexpr int PERSIST_MAX_M = 100;
 // and GIR_FLAG_BATCH_STREAMS not set.
 bool persistent_batch_supported(int nsys, const int64_t* n, const int64_t* lda, const gir_params* p);
 
+// True if the persistent kernel's modelled makespan on this device does not exceed the worker
+// streams' (the model and its GB300 constants are in gir.h, at gir_batch_solve).
+bool persistent_batch_preferred(int nsys, const int64_t* n);
+
 // The whole batch in one persistent launch (captured in a CUDA graph, launched on s); fills infos
 // and returns the worst status. Synchronises s.
 gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,

@@ -15,9 +15,11 @@
 //
 // Arithmetic, per system (the same formats as the single-system path):
 //  * A v of A~ in float-float from the split A = A_hi + A_lo (made once per system, after the LU,
-//    in the slot memory the LU's FP32 work matrix used);
-//  * both triangular solves of M^-1 in float-float on the u_f factors, 32-row blocks (a warp per
-//    row for the off-diagonal part, one warp for the diagonal block by shuffles);
+//    in the slot memory the LU's FP32 work matrix used; the halves interleaved by groups of four
+//    columns, so each row is one HBM stream);
+//  * both triangular solves of M^-1 in float-float on the u_f factors, 32-row blocks (two rows per
+//    warp for the off-diagonal part; the diagonal block through its float-float inverse, made once
+//    per system, with one refinement step);
 //  * the residual in FP64 or double-double; CGS2, norms and the small dense algebra in FP64 (the
 //    Givens step, cycle end and Cholesky QR are the same device functions the single-system path
 //    launches as kernels).
@@ -114,7 +116,6 @@ struct Smem {
     float2* ys;     // float-float y of the triangular solves (np)
     float* vh;      // float-float split of the A v input (np each)
     float* vl;
-    int* err;              // DEV_* flags of this CTA's current system
     double* close;  // cycle-end workspace (overlaps all of the above)
     int close_doubles;
 };
@@ -1120,8 +1121,7 @@ __device__ gir_status dev_status(int f) {
 }
 
 // Algorithm 4 on one system, by the whole CTA.
-__device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned char* dyn, Ctx& cx, double* red,
-                          int* s_err) {
+__device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned char* dyn, Ctx& cx, double* red) {
     const Sys sy = B.sys[sidx];
     gir_info* info = B.info + sidx;
     const int n = (int)sy.n;
@@ -1157,14 +1157,12 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
     }
     // a fresh small state (status, counters) for this system
     for (int i = threadIdx.x; i < (int)(sizeof(SmallState) / 4); i += NT) reinterpret_cast<int*>(sl.st)[i] = 0;
-    if (threadIdx.x == 0) *s_err = 0;
     __syncthreads();
     Smem sm;
     const int np = (n + 7) & ~7;
     sm.ys = reinterpret_cast<float2*>(dyn);
     sm.vh = reinterpret_cast<float*>(dyn + (size_t)8 * np);
     sm.vl = sm.vh + np;
-    sm.err = s_err;
     sm.close = reinterpret_cast<double*>(dyn);
     sm.close_doubles = DYN_BYTES / 8;
 
@@ -1225,7 +1223,6 @@ __device__ void solve_one(const Batch& B, const Slot& sl, int sidx, unsigned cha
     }
     const unsigned long long t2 = gtimer();
     __syncthreads();
-    if (*s_err && status != GIR_NONFINITE) status = dev_status(*s_err);
     if (threadIdx.x == 0) {
         info->status = status;
         info->ir_steps = ir_steps;
@@ -1244,7 +1241,6 @@ __global__ void __launch_bounds__(NT, 1) k_batch_persistent(const Batch B) {
     __shared__ Ctx cx;
     __shared__ double red[NW];
     __shared__ int s_q;
-    __shared__ int s_err;
     const Slot sl = B.slots[blockIdx.x];
     for (;;) {
         if (threadIdx.x == 0) s_q = atomicAdd(B.next, 1);
@@ -1252,7 +1248,7 @@ __global__ void __launch_bounds__(NT, 1) k_batch_persistent(const Batch B) {
         const int q = s_q;
         __syncthreads();
         if (q >= B.nsys) break;
-        solve_one(B, sl, B.order[q], dyn, cx, red, &s_err);
+        solve_one(B, sl, B.order[q], dyn, cx, red);
     }
 }
 
@@ -1271,6 +1267,26 @@ bool persistent_batch_supported(int nsys, const int64_t* n, const int64_t* lda, 
     return true;
 }
 
+bool persistent_batch_preferred(int nsys, const int64_t* n) {
+    // one CTA per system against the whole GPU per system (gir.h states the model and its constants)
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    double t1max = 0.0, t1sum = 0.0, tstreams = 0.0;
+    for (int i = 0; i < nsys; ++i) {
+        const double m = (double)n[i];
+        const double t1 = 8.7e-9 * m * m * m + 1.8e-5 * m * m;
+        t1max = t1 > t1max ? t1 : t1max;
+        t1sum += t1;
+        tstreams += 2.1 + 4.0e-7 * m * m;
+    }
+    const double tpers = t1max > t1sum / nsm ? t1max : t1sum / nsm;
+    return tpers <= tstreams;
+}
+
 gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* const* A, const int64_t* lda,
                                   const double* const* b, double* const* x, const gir_params* p, gir_info* infos,
                                   cudaStream_t s) {
@@ -1278,7 +1294,8 @@ gir_status persistent_batch_solve(int nsys, const int64_t* n, const double* cons
     if (p->m < 1 || p->m > PERSIST_MAX_M || p->k < 0 || p->k >= p->m || p->k > GIR_MAX_K || p->imax < 0 ||
         p->imax >= GIR_MAX_IR || !(p->tau >= 0.0) || (p->carry_mode != 0 && p->carry_mode != 1) ||
         (p->u != GIR_FP64 && p->u != GIR_FP32) || (p->ur != GIR_FP64 && p->ur != GIR_DD) ||
-        (p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_ADAPTIVE_K | GIR_FLAG_EIG_FP64 | GIR_FLAG_BASIS_FP32)) != 0)
+        (p->flags & ~(GIR_FLAG_AUTOTUNE | GIR_FLAG_ADAPTIVE_K | GIR_FLAG_EIG_FP64 | GIR_FLAG_BASIS_FP32 |
+                      GIR_FLAG_BATCH_PERSISTENT)) != 0)
         return GIR_INVALID_ARG;
     for (int i = 0; i < nsys; ++i)
         if (!A[i] || !b[i] || !x[i]) return GIR_INVALID_ARG;

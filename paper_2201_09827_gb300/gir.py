@@ -142,6 +142,7 @@ GIR_FLAG_ADAPTIVE_K = 0x8  # k = its_1 - 1 from the first refinement step (Secti
 GIR_FLAG_EIG_FP64 = 0x10  # harmonic Ritz eigenvalues by FP64 Hessenberg QR (default FP32)
 GIR_FLAG_BASIS_FP32 = 0x20  # Krylov and recycle basis vectors rounded to FP32 when stored
 GIR_FLAG_BATCH_STREAMS = 0x40  # batch_solve on the worker-stream pool instead of the persistent kernel
+GIR_FLAG_BATCH_PERSISTENT = 0x80  # batch_solve as the persistent kernel whatever the cost model prefers
 
 
 @dataclass
@@ -468,15 +469,19 @@ def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False, eng
     """Solve independent systems A_i x_i = b_i (gir_batch_solve).
 
     engine="auto": one persistent kernel launch for the whole batch where it applies (u_f bf16 or
-    fp16, ua fp64, no CW_BERR / SIR flag, n <= 8192, m <= 100), else the worker-stream pool;
-    engine="streams" forces the pool (GIR_FLAG_BATCH_STREAMS). autotune=True measures missing
-    size classes of the pool first (GIR_FLAG_AUTOTUNE)."""
-    if engine not in ("auto", "streams"):
-        raise ValueError(f"engine must be 'auto' or 'streams', not {engine!r}")
+    fp16, ua fp64, no CW_BERR / SIR flag, n <= 8192, m <= 100) and the cost model prefers it (many
+    systems), else the worker-stream pool; engine="persistent" forces the kernel
+    (GIR_FLAG_BATCH_PERSISTENT; GirError if it cannot take the batch), engine="streams" the pool
+    (GIR_FLAG_BATCH_STREAMS). autotune=True measures missing size classes of the pool first
+    (GIR_FLAG_AUTOTUNE)."""
+    if engine not in ("auto", "persistent", "streams"):
+        raise ValueError(f"engine must be 'auto', 'persistent' or 'streams', not {engine!r}")
     if autotune:
         params = replace(params, flags=params.flags | GIR_FLAG_AUTOTUNE)
     if engine == "streams":
         params = replace(params, flags=params.flags | GIR_FLAG_BATCH_STREAMS)
+    elif engine == "persistent":
+        params = replace(params, flags=params.flags | GIR_FLAG_BATCH_PERSISTENT)
     lib = load()
     nsys = len(As)
     ns = (C.c_int64 * nsys)(*[A.shape[0] for A in As])
@@ -488,6 +493,8 @@ def batch_solve(As, bs, params: Params, stream=None, autotune: bool = False, eng
     infos = (CInfo * nsys)()
     cp = params.c()
     st = lib.gir_batch_solve(nsys, ns, Ap, ldas, bp, xp, C.byref(cp), infos, _stream(stream))
+    if engine == "persistent" and st == GIR_UNSUPPORTED:
+        raise GirError(st, "gir_batch_solve: the persistent kernel cannot take this batch")
     return xs, [Info.from_c(infos[i]) for i in range(nsys)], st
 
 

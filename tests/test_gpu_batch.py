@@ -1,7 +1,8 @@
-"""The batch as one persistent kernel launch (gir_batch_solve's default engine): every system of an
-uneven batch against its own oracle solve, the same batch through the worker-stream engine, the
-other precision triples and options the kernel implements, per-system failure statuses, and a batch
-shaped like the 512-system workload (n up to 4096) checked by properties that hold at any size.
+"""The batch as one persistent kernel launch (gir_batch_solve with engine="persistent"; left to
+choose, the routing takes it for batches of many systems): every system of an uneven batch against
+its own oracle solve, the same batch through the worker-stream engine, the other precision triples
+and options the kernel implements, per-system failure statuses, and a batch shaped like the
+512-system workload (n up to 4096) checked by properties that hold at any size.
 
 Tolerances are those of the single-system parity tests: same convergence status, final normwise
 backward error <= 4x the oracle's (floored at the unit roundoff of u), total GMRES iterations within
@@ -67,7 +68,7 @@ def test_persistent_batch_parity_with_oracle(pkg):
     prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0,
                      max_its=300)
     before = pkg.launch_count()
-    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
     assert pkg.launch_count() - before == 1, "the whole batch is one kernel launch"
     assert st in (0, 1)
     op = _oracle(max_its=300)
@@ -82,7 +83,7 @@ def test_persistent_batch_reference_order(pkg):
     summation order of the LU: the order changes the iteration counts only where kappa u_f >> 1."""
     sizes, _, As, bs = _batch(12, 30, 1200, 2.0, 3.0, seed=9)
     prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0)
-    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
     op = _oracle(order="dot")
     for A, b, x, info in zip(As, bs, xs, infos):
         xo, io, _, _ = osolve(A, b, op)
@@ -95,7 +96,7 @@ def test_persistent_matches_stream_engine(pkg):
     sizes, _, As, bs = _batch(24, 40, 900, 2.0, 3.0, seed=11)
     prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=1e-15)
     Ad, bd = [cuda(A) for A in As], [cuda(b) for b in bs]
-    xp, ip, sp = pkg.batch_solve(Ad, bd, prm)
+    xp, ip, sp = pkg.batch_solve(Ad, bd, prm, engine="persistent")
     xq, iq, sq = pkg.batch_solve(Ad, bd, prm, engine="streams")
     assert sp == sq
     for A, b, x1, i1, x2, i2 in zip(As, bs, xp, ip, xq, iq):
@@ -112,7 +113,7 @@ def test_persistent_precision_triples(pkg, uf, u, ur):
     tau = 1e-4 if u == "fp32" else 1e-8
     sizes, _, As, bs = _batch(12, 20, 700, 2.0, 3.0, seed=13)
     prm = pkg.Params(uf=uf, u=u, ur=ur, m=30, k=8, tau=tau, imax=10, target_berr=-1.0)
-    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
     op = _oracle(uf=uf, u=u, ur=ur, tau=tau)
     for A, b, x, info in zip(As, bs, xs, infos):
         xo, io, _, _ = osolve(A, b, op)
@@ -134,7 +135,7 @@ def test_persistent_prolate_recycling(pkg):
     total = {}
     for k in (10, 0):
         prm = pkg.Params(uf="bf16", u="fp64", ur="dd", m=30, k=k, tau=1e-8, imax=10, target_berr=-1.0)
-        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
         op = _oracle(ur="dd", k=k)
         for A, b, x, info in zip(As, bs, xs, infos):
             xo, io, _, _ = osolve(A, b, op)
@@ -157,7 +158,7 @@ def test_persistent_carry_literal_and_adaptive_k(pkg):
              (dict(flags=pkg.GIR_FLAG_ADAPTIVE_K), dict(k_mode="knee"))]
     for gkw, okw in cases:
         prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0, **gkw)
-        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
         op = _oracle(**okw)
         for A, b, x, info in zip(As, bs, xs, infos):
             xo, io, _, _ = osolve(A, b, op)
@@ -174,8 +175,7 @@ def test_persistent_eig_fp64_and_fp32_basis(pkg):
     for flag, basis in ((gir.GIR_FLAG_EIG_FP64, None), (gir.GIR_FLAG_BASIS_FP32, "fp32")):
         prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=1e-15,
                          flags=flag)
-        assert pkg.batch_engine(sizes, prm) == "persistent"
-        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+        xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
         op = _oracle(target=1e-15, basis=basis)
         for A, b, x, info in zip(As, bs, xs, infos):
             xo, io, _, _ = osolve(A, b, op)
@@ -196,16 +196,18 @@ def test_persistent_status_paths(pkg):
     mats = [As_, good[0], An, good[1]]
     bs = [rhs_uniform(M.shape[0], i) for i, M in enumerate(mats)]
     prm = pkg.Params(uf="bf16", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0)
-    xs, infos, st = pkg.batch_solve([cuda(M) for M in mats], [cuda(b) for b in bs], prm)
+    xs, infos, st = pkg.batch_solve([cuda(M) for M in mats], [cuda(b) for b in bs], prm, engine="persistent")
     assert infos[0].status == gir.GIR_SINGULAR
     assert infos[2].status == gir.GIR_NONFINITE
     assert infos[1].status == gir.GIR_OK and infos[3].status == gir.GIR_OK
     assert st == max(gir.GIR_SINGULAR, gir.GIR_NONFINITE)
     prm1 = pkg.Params(uf="bf16", m=30, k=8, tau=1e-8, imax=1, target_berr=0.0)
-    xs, infos, st = pkg.batch_solve([cuda(good[0])], [cuda(bs[1])], prm1)
+    xs, infos, st = pkg.batch_solve([cuda(good[0])], [cuda(bs[1])], prm1, engine="persistent")
     assert st == gir.GIR_NOT_CONVERGED and infos[0].ir_steps == 1
     with pytest.raises(ValueError):
         pkg.batch_solve([cuda(good[0])], [cuda(bs[1])], prm1, engine="other")
+    with pytest.raises(gir.GirError):   # the kernel forced on a format it does not implement
+        pkg.batch_solve([cuda(good[0])], [cuda(bs[1])], pkg.Params(uf="e4m3"), engine="persistent")
 
 
 def test_persistent_batch_large_orders(pkg):
@@ -221,7 +223,7 @@ def test_persistent_batch_large_orders(pkg):
         xstars.append(xs_)
         bs.append(A @ xs_)
     prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0)
-    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm)
+    xs, infos, st = pkg.batch_solve([cuda(A) for A in As], [cuda(b) for b in bs], prm, engine="persistent")
     assert st == 0
     for A, b, x, xst, info, i in zip(As, bs, xs, xstars, infos, range(len(sizes))):
         xh = x.cpu().numpy()
