@@ -233,3 +233,29 @@ def test_persistent_batch_large_orders(pkg):
     i = sizes.index(2048)
     xo, io, _, _ = osolve(As[i], bs[i], _oracle())
     assert_parity(As[i], bs[i], xs[i].cpu().numpy(), infos[i], xo, io, "fp64")
+
+
+def test_persistent_batch_max_order(pkg):
+    """The kernel's order limit: n = 8192 and a ragged 7777 (both padded row pitches, the panel in
+    global memory, the float-float y and split v filling 128 KB of shared memory), kappa_2 = 1e2,
+    b = A x*, in one launch: both converge to the backward-error target (double-double residual on
+    the device) with Table 2's forward error against x*."""
+    from synth import randsvd_torch
+    sizes = [8192, 7777]
+    As, xst, bs = [], [], []
+    for i, n in enumerate(sizes):
+        A = randsvd_torch(n, 1e2, seed=600 + i, device="cuda")
+        g = torch.Generator(device="cuda")
+        g.manual_seed(700 + i)
+        x = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+        As.append(A)
+        xst.append(x)
+        bs.append(A @ x)
+    prm = pkg.Params(uf="bf16", u="fp64", ur="fp64", m=30, k=8, tau=1e-8, imax=10, target_berr=-1.0)
+    xs, infos, st = pkg.batch_solve(As, bs, prm, engine="persistent")
+    assert st == 0
+    for A, b, x, xs_, n in zip(As, bs, xs, xst, sizes):
+        eta, _ = pkg.backward_errors(A, x, b, "dd")
+        assert eta <= 4 * 2.0 ** -52
+        ferr = ((x - xs_).abs().max() / xs_.abs().max()).item()
+        assert ferr <= 10 * (2.0 ** -53 + n * 1e2 * 2.0 ** -53)
