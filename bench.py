@@ -310,7 +310,8 @@ def run_sweep(args, rank, world, local):
 
     n = args.n
     parts = set(args.only.split(",")) if args.only else {"randsvd", "prolate", "convdiff", "batch", "oracle"}
-    # (batch-small, the 24-system counter-capture workload, runs only when named)
+    # (batch-small, the 24-system counter-capture workload, and adjoint, the transposed solves against
+    # the forward ones, run only when named)
     # ---- headline matrix: kappa_2 x u_f, RGMRES-IR(50, 10) and the GMRES-IR(50) comparator
     for kappa in ((1e2, 1e4, 1e6, 1e8) if "randsvd" in parts else ()):
         A = randsvd_torch(n, kappa, seed=0, device=f"cuda:{local}")
@@ -463,6 +464,42 @@ def run_sweep(args, rank, world, local):
                         metric="ms for the whole batch of 24 systems"))
         del As, bs, xs_
 
+    # ---- the adjoint's transposed triangular solves beside the forward ones: one forward and one
+    # adjoint solve with the same factors, their phases timed by the library's trace (CUDA events on
+    # the solve's stream, per call), then K timed adjoint solves without the trace
+    if "adjoint" in parts:
+        names = ["trsv", "trsv adjoint", "gemv", "gemv adjoint"]
+        for label, A in (("conv-diff 5-point upwind N=100 (n=10000), Pe=50",
+                          torch.from_numpy(convdiff(100, 50.0)).to(dev)),
+                         ("randsvd n=16384, kappa_2=1e2", randsvd_torch(16384, 1e2, seed=0, device=f"cuda:{local}"))):
+            nn = A.shape[0]
+            b = torch.from_numpy(rhs_uniform(nn, 4)).to(dev)
+            prm = gir.Params(uf="bf16", u="fp64", ur="fp64", m=40, k=10, tau=1e-8, imax=10, target_berr=1e-15)
+            F = gir.Factorization(A, prm)
+            F.solve(A, b)
+            F.solve_adjoint(A, b)
+            torch.cuda.synchronize()
+            gir.trace_enable(True)
+            gir.trace_select(names)
+            x, info = F.solve(A, b)
+            lam, ia = F.solve_adjoint(A, b)
+            torch.cuda.synchronize()
+            rep = gir.trace_report()
+            gir.trace_enable(False)
+            ms, ts, _ = timed(lambda: F.solve_adjoint(A, b), max(1, args.steps), args.warmup)
+            per_call = {k: {"ms": v[0], "calls": v[1], "us_per_call": 1e3 * v[0] / max(v[1], 1)}
+                        for k, v in rep.items()}
+            emit(sweep_line(args, world, f"{label}, b~U(0,1); BF16 LU, RGMRES-IR(40,10); adjoint solve A^T lambda = b "
+                                         "with the forward solve's factors",
+                            {"n": nn, "uf": "bf16", "u": "fp64", "ur": "fp64", "m": 40, "k": 10}, ms, ts,
+                            {"forward_its": info.total_its, "adjoint_its": ia.total_its, "trace": per_call,
+                             "trsv_adjoint_over_forward": (per_call["trsv adjoint"]["us_per_call"]
+                                                           / per_call["trsv"]["us_per_call"])},
+                            metric="ms per adjoint solve (factors given)"))
+            F.close()
+            del A, b, x, lam
+            torch.cuda.empty_cache()
+
     # ---- the oracle at two sizes (validates the n^3 projection of the headline's cpu_baseline)
     if rank == 0 and not args.no_cpu and "oracle" in parts:
         proj, t1, t2, expo, i1, i2 = oracle_projection(args.n, args.sample_n, args.kappa, args.uf)
@@ -498,7 +535,8 @@ def main():
                          "backward, the 512-system batch and the oracle at two sizes; one JSON line per point")
     ap.add_argument("--only", default="",
                     help="with --sweep: a comma-separated subset of randsvd,prolate,convdiff,batch,oracle, or "
-                         "batch-small (24 systems for counter captures of the persistent kernel)")
+                         "batch-small (24 systems for counter captures of the persistent kernel) or adjoint "
+                         "(the transposed triangular solves of M^-T against the forward ones, by the trace)")
     args = ap.parse_args()
     rank, world, local = dist_env()
 

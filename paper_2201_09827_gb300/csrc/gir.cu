@@ -143,7 +143,7 @@ gir_status pool_alloc_t(T** p, size_t count, cudaStream_t s) {
 // still queued anywhere else (free_handle synchronises the device for that).
 void free_handle_on(gir_handle* h, cudaStream_t s) {
     if (!h) return;
-    void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.EL, h->trsv.EU, h->trsv.perm, h->trsv.z, h->trsv.y1,
+    void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.EL, h->trsv.EU, h->trsv.EUt, h->trsv.ELt, h->trsv.perm, h->trsv.z, h->trsv.y1,
                     h->trsv.y2, h->trsv.ready, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
                     h->scratch, h->st, h->qh, h->dsc, h->dflags, h->Ahi, h->Alo, h->vsplit,
@@ -316,9 +316,10 @@ gir_status arnoldi_step(gir_handle* h, const double* A, int64_t lda, int trans, 
     const int64_t n = h->n;
     double* vj = V(h, j);
     double* w = V(h, j + 1);
-    { int tslot_ = trace_begin(s, "gemv");
+    { const char* ph_ = trans ? "gemv adjoint" : "gemv";
+    int tslot_ = trace_begin(s, ph_);
     GIR_TRY(launch_op_gemv(h, A, lda, vj, h->vtmp, trans, s));
-    trace_end(tslot_, "gemv", s); }
+    trace_end(tslot_, ph_, s); }
     { int tslot_ = trace_begin(s, "minv");
     GIR_TRY(apply_minv_op(h, w, trans, s));
     trace_end(tslot_, "minv", s); }
@@ -693,6 +694,8 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     ALLOC(h->trsv.DU, (size_t)nblk * TRSV_BLOCK * TRSV_BLOCK);
     ALLOC(h->trsv.EL, (size_t)nblk * TRSV_BLOCK * TRSV_BLOCK);
     ALLOC(h->trsv.EU, (size_t)nblk * TRSV_BLOCK * TRSV_BLOCK);
+    ALLOC(h->trsv.EUt, (size_t)nblk * TRSV_BLOCK * TRSV_BLOCK);
+    ALLOC(h->trsv.ELt, (size_t)nblk * TRSV_BLOCK * TRSV_BLOCK);
     ALLOC(h->trsv.perm, n);
     ALLOC(h->trsv.z, n);
     ALLOC(h->trsv.y1, n);

@@ -63,17 +63,20 @@ __global__ void __launch_bounds__(TB) k_diag_inv(const uint16_t* __restrict__ LU
     }
 }
 
-// E[I] = D[I] T_{I,J} with J = I - 1 (L, upper == 0) or I + 1 (U, upper == 1): the product of the
-// diagonal-block inverse with the block the forward solve meets last. Float-float dot products of
-// the float-float D with the u_f tile (exact in FP32), stored as float-float (row-major b x b per
-// block); blocks without such a neighbour, and rows/columns beyond n, are zero.
+// E[I] = D'[I] T'_{I,J}: the product of the diagonal-block inverse with the block that a solve meets
+// last, J = I + 1 (next == 1: backward order) or I - 1 (next == 0: forward order). For M^-1
+// (trans == 0) D' and T' are the stored blocks (L solve: DL, J = I - 1; U solve: DU, J = I + 1); for
+// M^-T (trans == 1) they are the transposes (U^T solve: DU^T with T'_{I,J} = U_{J,I}^T, J = I - 1;
+// L^T solve: DL^T with T'_{I,J} = L_{J,I}^T, J = I + 1). Float-float dot products of the float-float
+// D with the u_f tile (exact in FP32), stored as float-float (row-major b x b per block, in the
+// solve's own orientation); blocks without such a neighbour, and rows/columns beyond n, are zero.
 __global__ void __launch_bounds__(256) k_diag_e(const uint16_t* __restrict__ LU, int64_t ldl, int64_t n, int fmt,
-                                                int upper, const float2* __restrict__ D, int nblk,
+                                                int next, int trans, const float2* __restrict__ D, int nblk,
                                                 float2* __restrict__ E) {
     __shared__ float2 Ds[TB][TB + 1];
     __shared__ uint16_t Ts[TB][TB + 2];
     const int I = blockIdx.x;
-    const int J = upper ? I + 1 : I - 1;
+    const int J = next ? I + 1 : I - 1;
     const int tid = threadIdx.x;
     float2* Eb = E + (int64_t)I * TB * TB;
     if (J < 0 || J >= nblk) {
@@ -82,9 +85,15 @@ __global__ void __launch_bounds__(256) k_diag_e(const uint16_t* __restrict__ LU,
     }
     for (int e = tid; e < TB * TB; e += 256) {
         const int i = e / TB, c = e % TB;
-        Ds[i][c] = D[(int64_t)I * TB * TB + e];
-        const int64_t gi = (int64_t)I * TB + i, gc = (int64_t)J * TB + c;
-        Ts[i][c] = (gi < n && gc < n) ? LU[gi * ldl + gc] : (uint16_t)0;   // 0 is +0 in both formats
+        if (!trans) {
+            Ds[i][c] = D[(int64_t)I * TB * TB + e];
+            const int64_t gi = (int64_t)I * TB + i, gc = (int64_t)J * TB + c;
+            Ts[i][c] = (gi < n && gc < n) ? LU[gi * ldl + gc] : (uint16_t)0;   // 0 is +0 in both formats
+        } else {
+            Ds[c][i] = D[(int64_t)I * TB * TB + e];
+            const int64_t gr = (int64_t)J * TB + c, gc = (int64_t)I * TB + i;
+            Ts[i][c] = (gr < n && gc < n) ? LU[gr * ldl + gc] : (uint16_t)0;
+        }
     }
     __syncthreads();
     const int r = tid >> 2, q = tid & 3;
@@ -106,17 +115,9 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// LOWER: forward order (block I depends on J < I); otherwise backward (J > I).
-// TRANS: the tile of block (I, J) is the transpose of stored tile (J, I).
-// Input zin: FP64 (zin64) or float-float (zin_ff); output: float-float yout, published
-// element by element: yout starts as the all-ones pattern (an FP32 NaN no computation
-// writes) and each element is written with one 64-bit store, so a consumer polls the data
-// itself instead of a separate flag. The tile of the next dependency is loaded into
-// registers before waiting, and the diagonal-block inverse is staged in shared memory.
+// Output y (float-float) is published element by element: y starts as the all-ones pattern (an
+// FP32 NaN no computation writes) and each element is written with one 64-bit store, so a
+// consumer polls the data itself instead of a separate flag.
 constexpr unsigned long long Y_EMPTY = 0xFFFFFFFFFFFFFFFFull;
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
@@ -131,149 +132,6 @@ __device__ __forceinline__ unsigned long long pack_ff(float h, float l) {
     if (h != h) h = __int_as_float(0x7fc00000);  // canonical NaN, never the empty pattern
     if (l != l) l = 0.0f;
     return ((unsigned long long)__float_as_uint(l) << 32) | (unsigned long long)__float_as_uint(h);
-}
-
-template <bool LOWER, bool TRANS>
-__global__ void __launch_bounds__(256) k_trsv(const uint16_t* __restrict__ LU, int64_t ldl, int fmt,
-                                              const float2* __restrict__ D, int64_t n, int nblk,
-                                              const double* __restrict__ zin64, const float2* __restrict__ zin_ff,
-                                              float2* __restrict__ yout, int* __restrict__ ready,
-                                              unsigned long long* __restrict__ ticket_ctr, unsigned long long base,
-                                              int epoch, int* __restrict__ abort_flag, int* __restrict__ flags) {
-    __shared__ float acc_h[TB], acc_l[TB];
-    __shared__ float yj_h[TB], yj_l[TB];
-    __shared__ float red_h[4][TB], red_l[4][TB];
-    __shared__ float2 Ds[TB][TB + 1];
-    __shared__ int s_ticket, s_abort;
-    (void)ready;
-    (void)epoch;
-    unsigned long long* ybits = reinterpret_cast<unsigned long long*>(yout);
-
-    const int tid = threadIdx.x;
-    if (tid == 0) s_ticket = (int)(atomicAdd(ticket_ctr, 1ULL) - base);
-    __syncthreads();
-    const int t = s_ticket;
-    if (t < 0 || t >= nblk) {
-        if (tid == 0) { atomicOr(flags, DEV_TIMEOUT); atomicExch(abort_flag, 1); }
-        return;
-    }
-    const int I = LOWER ? t : (nblk - 1 - t);
-    const int64_t r0 = (int64_t)I * TB;
-    {
-        const float2* Dblk = D + (int64_t)I * TB * TB;
-        for (int e = tid; e < TB * TB; e += 256) Ds[e / TB][e % TB] = Dblk[e];
-    }
-    if (tid < TB) {
-        int64_t gi = r0 + tid;
-        float h = 0.0f, l = 0.0f;
-        if (gi < n) {
-            if (zin64) {
-                double v = zin64[gi];
-                h = __double2float_rn(v);
-                l = __double2float_rn(v - (double)h);
-            } else {
-                float2 v = zin_ff[gi];
-                h = v.x;
-                l = v.y;
-            }
-        }
-        acc_h[tid] = h;
-        acc_l[tid] = l;
-    }
-    if (tid == 0) s_abort = 0;
-    __syncthreads();
-
-    const int r = TRANS ? (tid & 63) : (tid >> 2);
-    const int q = TRANS ? (tid >> 6) : (tid & 3);
-    float tv[16];
-    auto load_tile = [&](int J) {
-        const int64_t c0 = (int64_t)J * TB;
-        if (!TRANS) {
-            const int64_t gi = r0 + r;
-#pragma unroll
-            for (int cc = 0; cc < 16; ++cc) {
-                int64_t gc = c0 + q * 16 + cc;
-                tv[cc] = (gi < n && gc < n) ? uf_to_float(LU[gi * ldl + gc], fmt) : 0.0f;
-            }
-        } else {
-            const int64_t gcol = r0 + r;
-#pragma unroll
-            for (int cc = 0; cc < 16; ++cc) {
-                int64_t grow = c0 + q * 16 + cc;
-                tv[cc] = (gcol < n && grow < n) ? uf_to_float(LU[grow * ldl + gcol], fmt) : 0.0f;
-            }
-        }
-    };
-    const int ndep = LOWER ? I : (nblk - 1 - I);
-    for (int step = 0; step < ndep; ++step) {
-        const int J = LOWER ? step : (nblk - 1 - step);
-        const int64_t c0 = (int64_t)J * TB;
-        load_tile(J);  // independent of y: issued before waiting
-        if (tid < TB) {
-            const int64_t gc = c0 + tid;
-            unsigned long long v = 0ull;
-            if (gc < n) {
-                long long spins = 0;
-                while ((v = ld_relaxed_u64(ybits + gc)) == Y_EMPTY) {
-                    if (((spins & 1023) == 0) && ld_acquire(abort_flag)) { s_abort = 1; break; }
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(flags, DEV_TIMEOUT);
-                        atomicExch(abort_flag, 1);
-                        s_abort = 1;
-                        break;
-                    }
-                }
-            }
-            yj_h[tid] = __uint_as_float((unsigned)(v & 0xffffffffull));
-            yj_l[tid] = __uint_as_float((unsigned)(v >> 32));
-        }
-        __syncthreads();
-        if (s_abort) break;
-        float sh = 0.0f, sl = 0.0f;
-#pragma unroll
-        for (int cc = 0; cc < 16; ++cc) {
-            int c = q * 16 + cc;
-            ff_acc_prod1(sh, sl, tv[cc], yj_h[c], yj_l[c]);
-        }
-        red_h[q][r] = sh;
-        red_l[q][r] = sl;
-        __syncthreads();
-        if (tid < TB) {
-            float h = red_h[0][tid], l = red_l[0][tid];
-            ff_acc_add(h, l, red_h[1][tid], red_l[1][tid]);
-            ff_acc_add(h, l, red_h[2][tid], red_l[2][tid]);
-            ff_acc_add(h, l, red_h[3][tid], red_l[3][tid]);
-            float ah = acc_h[tid], al = acc_l[tid];
-            ff_acc_add(ah, al, -h, -l);
-            ff ns = ff_norm(ah, al);
-            acc_h[tid] = ns.h;
-            acc_l[tid] = ns.l;
-        }
-        __syncthreads();
-    }
-
-    // y_I = D_I acc (TRANS: D_I^T acc), D staged in shared memory
-    {
-        float sh = 0.0f, sl = 0.0f;
-#pragma unroll
-        for (int cc = 0; cc < 16; ++cc) {
-            int c = q * 16 + cc;
-            float2 d = TRANS ? Ds[c][r] : Ds[r][c];
-            ff_acc_prod2(sh, sl, d.x, d.y, acc_h[c], acc_l[c]);
-        }
-        red_h[q][r] = sh;
-        red_l[q][r] = sl;
-        __syncthreads();
-        if (tid < TB) {
-            float h = red_h[0][tid], l = red_l[0][tid];
-            ff_acc_add(h, l, red_h[1][tid], red_l[1][tid]);
-            ff_acc_add(h, l, red_h[2][tid], red_l[2][tid]);
-            ff_acc_add(h, l, red_h[3][tid], red_l[3][tid]);
-            ff ns = ff_norm(h, l);
-            int64_t gi = r0 + tid;
-            if (gi < n) st_relaxed_u64(ybits + gi, s_abort ? pack_ff(0.0f, 0.0f) : pack_ff(ns.h, ns.l));
-        }
-    }
 }
 
 // ------------------------------------------------------------------ pre/post scaling
@@ -389,8 +247,14 @@ __device__ __forceinline__ void tf_st_async_u64(uint32_t addr, unsigned long lon
                  : "memory");
 }
 
-template <bool LOWER>
-__global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ LU, int64_t ldl, int fmt,
+// TRANS: the solve of M^-T meets block (I, J) as the transpose of stored block (J, I). A thread then
+// copies 32 bytes of row r of the stored tile (J, I) (contiguous, like the forward case), which
+// contribute to 16 different solution rows: it keeps 16 float-float partial sums across all the
+// dependencies, and the 64 rows of the tile are summed once per block (shuffles within a warp, one
+// shared-memory pass across warps) while the block still waits for its last dependency. D and E
+// arrive in the solve's own orientation for E and stored orientation for D (read transposed).
+template <bool LOWER, bool TRANS>
+__device__ __forceinline__ void trsv_cluster_body(const uint16_t* __restrict__ LU, int64_t ldl, int fmt,
                                                   const float2* __restrict__ D, const float2* __restrict__ E,
                                                   int64_t n, int nblk,
                                                   const double* __restrict__ zin64, const float2* __restrict__ zin_ff,
@@ -404,6 +268,7 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
         reinterpret_cast<unsigned long long (*)[TB]>(tf_dyn + (size_t)TF_STAGES * 2 * 256 * sizeof(uint4));
     __shared__ float2 yj[2][TB + 2];                          // padded by one entry per 32
     __shared__ float2 accs[TB + 2];
+    __shared__ float2 wred[TRANS ? 8 : 1][TB + 2];              // TRANS: per-warp sums of the tile rows
     __shared__ __align__(8) unsigned long long cbar[TF_MAXCL];               // one per lower rank
     __shared__ __align__(16) unsigned long long ycl[TF_MAXCL][TB];           // blocks of lower ranks
     __shared__ int s_ticket, s_abort;
@@ -450,12 +315,24 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
         const int first_local = kc * csize;      // dependencies from here on come from this cluster
         // this thread's 16 entries of the diagonal-block inverse, loaded now: the product with them
         // follows the last dependency and is on the critical path of the solve
+        // (TRANS: loaded after the dependency loop, which holds 16 partial sums in registers)
         float4 dreg[8];
-        {
-            const float4* drow = reinterpret_cast<const float4*>(D + ((int64_t)I * TB + r) * TB + q * 16);
+        auto load_d = [&]() {
+            if (!TRANS) {
+                const float4* drow = reinterpret_cast<const float4*>(D + ((int64_t)I * TB + r) * TB + q * 16);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) dreg[k] = drow[k];
-        }
+                for (int k = 0; k < 8; ++k) dreg[k] = drow[k];
+            } else {
+                // entries (q*16 + c, r) of the stored inverse: row r of its transpose
+                const float2* dcol = D + ((int64_t)I * TB + q * 16) * TB + r;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float2 d0 = dcol[(2 * k) * TB], d1 = dcol[(2 * k + 1) * TB];
+                    dreg[k] = make_float4(d0.x, d0.y, d1.x, d1.y);
+                }
+            }
+        };
+        if (!TRANS) load_d();
         // and its 16 entries of E = D_I T_{I,J} for the last dependency J: once y_J arrives, only
         // y_I = w - E y_J remains, with w = D_I (z_I - sum over the other dependencies) formed
         // while the block still waits
@@ -470,13 +347,15 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
         // L2 by cp.async.cg): a block published before its step comes up costs no round trip
         auto issue = [&](int step, int st) {
             const int J = dep_block(step);
-            const int64_t c0 = (int64_t)J * TB + q * 16;
+            // forward: row gi of the stored tile (I, J); TRANS: row r of the stored tile (J, I)
+            const int64_t trow = TRANS ? (int64_t)J * TB + r : gi;
+            const int64_t c0 = (TRANS ? r0 : (int64_t)J * TB) + q * 16;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int64_t cc = c0 + 8 * k;
                 int bytes = 0;
-                if (gi < n && cc < n && step < ndep - 1) bytes = (int)(2 * gmin<int64_t>(8, n - cc));
-                const uint16_t* src = bytes ? LU + gi * ldl + cc : LU;
+                if (trow < n && cc < n && step < ndep - 1) bytes = (int)(2 * gmin<int64_t>(8, n - cc));
+                const uint16_t* src = bytes ? LU + trow * ldl + cc : LU;
                 tf_cp_async16(&ring[st][k][tid], src, bytes);
             }
             if (step < first_local && tid < TB / 2) {
@@ -539,6 +418,9 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
                 ff_acc_add(sh, sl, oh, ol);
             }
         };
+        float part_h[TRANS ? 16 : 1], part_l[TRANS ? 16 : 1];   // TRANS: sums for rows q*16 + c
+#pragma unroll
+        for (int c = 0; c < (TRANS ? 16 : 1); ++c) part_h[c] = part_l[c] = 0.0f;
 #pragma unroll
         for (int p = 0; p < TF_AHEAD; ++p) {
             if (p < ndep) issue(p, p);
@@ -554,6 +436,30 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
             else wait_global(dep_block(step), buf, st);
             __syncthreads();
             if (s_abort) break;
+            if (TRANS) {
+                const float2 yv = yj[buf][pad(r)];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint4 v = ring[st][k][tid];
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int c = 8 * k + 2 * m;
+                        ff_acc_prod1(part_h[c], part_l[c], uf_to_float((uint16_t)(w[m] & 0xffffu), fmt), yv.x, yv.y);
+                        ff_acc_prod1(part_h[c + 1], part_l[c + 1], uf_to_float((uint16_t)(w[m] >> 16), fmt), yv.x,
+                                     yv.y);
+                    }
+                }
+                if ((step & 3) == 3) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const ff ns = ff_norm(part_h[c], part_l[c]);
+                        part_h[c] = ns.h;
+                        part_l[c] = ns.l;
+                    }
+                }
+                continue;
+            }
             // two partial sums: half-length dependency chains
             float sh = 0.0f, sl = 0.0f, th = 0.0f, tl = 0.0f;
 #pragma unroll
@@ -574,6 +480,35 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
             const ff ns = ff_norm(ah, al);
             ah = ns.h;
             al = ns.l;
+        }
+        if (TRANS) {
+            load_d();
+            // sum the partial sums over the 64 tile rows: the 8 rows of a warp by shuffles, then the
+            // 8 warps through shared memory into the accumulator of row r (threads with q == 0)
+#pragma unroll
+            for (int o = 4; o <= 16; o <<= 1) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, part_h[c], o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, part_l[c], o);
+                    ff_acc_add(part_h[c], part_l[c], oh, ol);
+                }
+            }
+            if ((tid & 31) < 4) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) wred[tid >> 5][pad(q * 16 + c)] = make_float2(part_h[c], part_l[c]);
+            }
+            __syncthreads();
+            if (q == 0) {
+#pragma unroll
+                for (int wp = 0; wp < 8; ++wp) {
+                    const float2 v = wred[wp][pad(r)];
+                    ff_acc_add(ah, al, -v.x, -v.y);
+                }
+                const ff ns = ff_norm(ah, al);
+                ah = ns.h;
+                al = ns.l;
+            }
         }
         // w = D_I acc (acc holds everything but the last dependency)
         if (q == 0) accs[pad(r)] = make_float2(ah, al);
@@ -634,6 +569,25 @@ __global__ void __launch_bounds__(256) k_trsv_fwd(const uint16_t* __restrict__ L
     tf_cluster_sync();
 }
 
+#define TRSV_CLUSTER_ARGS                                                                                         \
+    const uint16_t *__restrict__ LU, int64_t ldl, int fmt, const float2 *__restrict__ D,                        \
+        const float2 *__restrict__ E, int64_t n, int nblk, const double *__restrict__ zin64,                    \
+        const float2 *__restrict__ zin_ff, float2 *__restrict__ yout, unsigned long long *__restrict__ ticket_ctr, \
+        unsigned long long base, int *__restrict__ abort_flag, int *__restrict__ flags
+// M^-1's solves: L (LOWER) then U
+template <bool LOWER>
+__global__ void __launch_bounds__(256) k_trsv_fwd(TRSV_CLUSTER_ARGS) {
+    trsv_cluster_body<LOWER, false>(LU, ldl, fmt, D, E, n, nblk, zin64, zin_ff, yout, ticket_ctr, base, abort_flag,
+                                    flags);
+}
+// M^-T's solves: U^T (LOWER: forward order) then L^T (backward order)
+template <bool LOWER>
+__global__ void __launch_bounds__(256) k_trsv_adj(TRSV_CLUSTER_ARGS) {
+    trsv_cluster_body<LOWER, true>(LU, ldl, fmt, D, E, n, nblk, zin64, zin_ff, yout, ticket_ctr, base, abort_flag,
+                                   flags);
+}
+#undef TRSV_CLUSTER_ARGS
+
 // ------------------------------------------------------------------ host side
 gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n, int fmt, cudaStream_t s) {
     st.n = n;
@@ -643,13 +597,15 @@ gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n,
     st.ldl = ldl;
     const int smem = 2 * TB * (TB + 1) * (int)sizeof(double);
     GIR_CUDA_TRY(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TF_DYN_SMEM));
-    GIR_CUDA_TRY(cudaFuncSetAttribute(k_trsv_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TF_DYN_SMEM));
+    const void* kernels[4] = {(const void*)k_trsv_fwd<true>, (const void*)k_trsv_fwd<false>,
+                              (const void*)k_trsv_adj<true>, (const void*)k_trsv_adj<false>};
+    for (const void* fn : kernels)
+        GIR_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TF_DYN_SMEM));
     if (st.cluster > 8) {
         // 16-CTA clusters are a non-portable size: use them only where the device can hold one
         int ok = 1;
-        for (int lower = 0; lower < 2 && ok; ++lower) {
-            const void* fn = lower ? (const void*)k_trsv_fwd<true> : (const void*)k_trsv_fwd<false>;
+        for (int kf = 0; kf < 4 && ok; ++kf) {
+            const void* fn = kernels[kf];
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
                 ok = 0;
                 break;
@@ -675,38 +631,23 @@ gir_status trsv_setup(TrsvState& st, const uint16_t* LU, int64_t ldl, int64_t n,
     }
     count_launch(), k_diag_inv<<<st.nblk, TB, smem, s>>>(LU, ldl, n, fmt, 0, st.DL);
     count_launch(), k_diag_inv<<<st.nblk, TB, smem, s>>>(LU, ldl, n, fmt, 1, st.DU);
-    count_launch(), k_diag_e<<<st.nblk, 256, 0, s>>>(LU, ldl, n, fmt, 0, st.DL, st.nblk, st.EL);
-    count_launch(), k_diag_e<<<st.nblk, 256, 0, s>>>(LU, ldl, n, fmt, 1, st.DU, st.nblk, st.EU);
+    count_launch(), k_diag_e<<<st.nblk, 256, 0, s>>>(LU, ldl, n, fmt, 0, 0, st.DL, st.nblk, st.EL);
+    count_launch(), k_diag_e<<<st.nblk, 256, 0, s>>>(LU, ldl, n, fmt, 1, 0, st.DU, st.nblk, st.EU);
+    st.et_ready = false;   // the transposed solves' E blocks follow on their first use
     GIR_CUDA_TRY(cudaGetLastError());
     return GIR_OK;
 }
 
 template <bool LOWER, bool TRANS>
-static gir_status run_trsv(TrsvState& st, const float2* D, const double* z64, const float2* zff, float2* y,
-                           int* flags, cudaStream_t s) {
-    int* ready = st.ready;
-    unsigned long long base = st.tickets;
-    st.tickets += (unsigned long long)st.nblk;
-    int epoch = ++st.epoch;
-    GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
-    const int tslot = trace_begin(s, "trsv");
-    count_launch(), k_trsv<LOWER, TRANS><<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, st.fmt, D, st.n, st.nblk, z64, zff, y, ready,
-                                                 st.ticket_ctr, base, epoch, st.abort_flag, flags);
-    trace_end(tslot, "trsv", s);
-    st.calls++;
-    GIR_CUDA_TRY(cudaGetLastError());
-    return GIR_OK;
-}
-
-template <bool LOWER>
-static gir_status run_trsv_fwd(TrsvState& st, const float2* D, const float2* E, const double* z64, const float2* zff,
+static gir_status run_trsv_cl(TrsvState& st, const float2* D, const float2* E, const double* z64, const float2* zff,
                                float2* y, int* flags, cudaStream_t s) {
     const int csize = st.cluster;
     const int nclu = (st.nblk + csize - 1) / csize;
     unsigned long long base = st.tickets;
     st.tickets += (unsigned long long)nclu;   // one ticket per cluster
     GIR_CUDA_TRY(cudaMemsetAsync(y, 0xFF, (size_t)st.n * sizeof(float2), s));
-    const int tslot = trace_begin(s, "trsv");
+    const char* name = TRANS ? "trsv adjoint" : "trsv";
+    const int tslot = trace_begin(s, name);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclu * csize), 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -720,9 +661,9 @@ static gir_status run_trsv_fwd(TrsvState& st, const float2* D, const float2* E, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    GIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_trsv_fwd<LOWER>, st.LU, st.ldl, st.fmt, D, E, st.n, st.nblk, z64, zff, y,
+    GIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, TRANS ? k_trsv_adj<LOWER> : k_trsv_fwd<LOWER>, st.LU, st.ldl, st.fmt, D, E, st.n, st.nblk, z64, zff, y,
                                     st.ticket_ctr, base, st.abort_flag, flags));
-    trace_end(tslot, "trsv", s);
+    trace_end(tslot, name, s);
     st.calls++;
     return GIR_OK;
 }
@@ -733,14 +674,20 @@ gir_status apply_minv(TrsvState& st, const double* w, double* out, const double*
     const int g = (int)gmin<int64_t>((n + 255) / 256, 1024);
     if (!trans) {
         count_launch(), k_minv_pre<<<g, 256, 0, s>>>(w, st.perm, R, n, st.z);
-        GIR_TRY((run_trsv_fwd<true>(st, st.DL, st.EL, st.z, nullptr, st.y1, flags, s)));
-        GIR_TRY((run_trsv_fwd<false>(st, st.DU, st.EU, nullptr, st.y1, st.y2, flags, s)));
+        GIR_TRY((run_trsv_cl<true, false>(st, st.DL, st.EL, st.z, nullptr, st.y1, flags, s)));
+        GIR_TRY((run_trsv_cl<false, false>(st, st.DU, st.EU, nullptr, st.y1, st.y2, flags, s)));
         count_launch(), k_minv_post<<<g, 256, 0, s>>>(st.y2, S, mu, n, round32, out);
     } else {
+        if (!st.et_ready) {
+            // E'[I] = DU[I]^T U[I-1, I]^T (U^T solve) and DL[I]^T L[I+1, I]^T (L^T solve)
+            count_launch(), k_diag_e<<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, n, st.fmt, 0, 1, st.DU, st.nblk, st.EUt);
+            count_launch(), k_diag_e<<<st.nblk, 256, 0, s>>>(st.LU, st.ldl, n, st.fmt, 1, 1, st.DL, st.nblk, st.ELt);
+            st.et_ready = true;
+        }
         count_launch(), k_minv_pre_t<<<g, 256, 0, s>>>(w, S, n, st.z);
         // M^-T = mu R P^T L^-T U^-T S: first U^T (lower), then L^T (upper, unit)
-        GIR_TRY((run_trsv<true, true>(st, st.DU, st.z, nullptr, st.y1, flags, s)));
-        GIR_TRY((run_trsv<false, true>(st, st.DL, nullptr, st.y1, st.y2, flags, s)));
+        GIR_TRY((run_trsv_cl<true, true>(st, st.DU, st.EUt, st.z, nullptr, st.y1, flags, s)));
+        GIR_TRY((run_trsv_cl<false, true>(st, st.DL, st.ELt, nullptr, st.y1, st.y2, flags, s)));
         count_launch(), k_minv_post_t<<<g, 256, 0, s>>>(st.y2, st.perm, R, mu, n, round32, out);
     }
     GIR_CUDA_TRY(cudaGetLastError());

@@ -17,6 +17,9 @@ struct TrsvState {
     float2* DU = nullptr;            // inverses of the upper diagonal blocks
     float2* EL = nullptr;            // DL[I] L[I, I-1] (float-float), the last step of the L solve
     float2* EU = nullptr;            // DU[I] U[I, I+1], the last step of the U solve
+    float2* EUt = nullptr;           // DU[I]^T U[I-1, I]^T, the last step of the U^T solve (M^-T)
+    float2* ELt = nullptr;           // DL[I]^T L[I+1, I]^T, the last step of the L^T solve
+    bool et_ready = false;           // EUt, ELt hold the current factors (formed on first use)
     int* perm = nullptr;             // row permutation P (from the interchanges)
     double* z = nullptr;             // scaled/permuted input (FP64)
     float2* y1 = nullptr;            // intermediate and final solutions (float-float)
