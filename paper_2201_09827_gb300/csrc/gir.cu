@@ -144,7 +144,7 @@ gir_status pool_alloc_t(T** p, size_t count, cudaStream_t s) {
 void free_handle_on(gir_handle* h, cudaStream_t s) {
     if (!h) return;
     void* ptrs[] = {h->LU, h->ipiv, h->R, h->S, h->trsv.DL, h->trsv.DU, h->trsv.EL, h->trsv.EU, h->trsv.EUt, h->trsv.ELt, h->trsv.perm, h->trsv.z, h->trsv.y1,
-                    h->trsv.y2, h->trsv.ready, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
+                    h->trsv.y2, h->trsv.ticket_ctr, h->trsv.abort_flag, h->Wb, h->fwd.U, h->fwd.C,
                     h->adj.U, h->adj.C, h->Ucur, h->Ctmp, h->Utmp, h->vtmp, h->r, h->dvec, h->cvec, h->rr,
                     h->scratch, h->st, h->qh, h->dsc, h->dflags, h->Ahi, h->Alo, h->vsplit,
                     h->ddst.DL, h->ddst.DU, h->ddst.z, h->ddst.y1, h->ddst.y2, h->ddst.w, h->ddst.part,
@@ -700,7 +700,6 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
     ALLOC(h->trsv.z, n);
     ALLOC(h->trsv.y1, n);
     ALLOC(h->trsv.y2, n);
-    ALLOC(h->trsv.ready, nblk);
     ALLOC(h->trsv.ticket_ctr, 1);
     ALLOC(h->trsv.abort_flag, 1);
     h->ldb = (n + 1) / 2 * 2;
@@ -780,7 +779,6 @@ gir_status gir_factor(const double* A, int64_t n, int64_t lda, const gir_params*
         return st;
     }
     cudaMemsetAsync(h->dflags, 0, 4 * sizeof(int), s);
-    cudaMemsetAsync(h->trsv.ready, 0, nblk * sizeof(int), s);
     cudaMemsetAsync(h->trsv.ticket_ctr, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(h->trsv.abort_flag, 0, sizeof(int), s);
     cudaMemsetAsync(h->st, 0, sizeof(SmallState), s);

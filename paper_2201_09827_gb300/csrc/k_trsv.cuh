@@ -24,11 +24,9 @@ struct TrsvState {
     double* z = nullptr;             // scaled/permuted input (FP64)
     float2* y1 = nullptr;            // intermediate and final solutions (float-float)
     float2* y2 = nullptr;
-    int* ready = nullptr;            // per-block ready flags (epoch numbers)
     unsigned long long* ticket_ctr = nullptr;
     int* abort_flag = nullptr;
     unsigned long long tickets = 0;  // host mirror of the ticket counter
-    int epoch = 0;
     int calls = 0;
     int cluster = 16;                // CTAs per cluster of the forward solves (16, or 8 where 16 cannot run)
 };
